@@ -1,0 +1,187 @@
+/*
+ * cbfs.h -- C ABI of the GB300 Cluster-BFS library (libcbfs.so).
+ *
+ * Cluster-BFS (C-BFS) runs one breadth-first search from a whole cluster S
+ * of k <= 64 sources whose pairwise distances are at most d (the paper
+ * "Parallel Cluster-BFS and Applications to Shortest Paths", Section 3).
+ * For every vertex v it returns the cluster distance vector
+ * <S_v[0..d], Delta_v> of Section 3.1:
+ *   Delta_v  = min over s in S of delta(s, v),
+ *   S_v[i]   = { s in S : delta(s, v) = Delta_v + i },  i = 0..d,
+ * with each subset stored as a 64-bit word, bit j standing for S[j]
+ * (least significant bit = S[0]).  By Corollary 1 the d+1 subsets cover S
+ * for every reachable v, so only S_v[0..d-1] are stored; S_v[d] is
+ * ALL & ~(S_v[0] | ... | S_v[d-1]) when Delta_v is finite (ALL = the k low
+ * bits) and empty otherwise.
+ *
+ * Output format (caller-allocated device memory; the library never
+ * allocates outputs):
+ *   dist  uint8_t [n]      Delta_v, 0xFF when no source reaches v;
+ *   masks uint64_t[d][n]   masks[i*n + v] = S_v[i]   (d = 0: may be NULL).
+ * Batched calls use [C][n] and [C][d][n] with cluster c at offset c*n and
+ * c*d*n.
+ *
+ * Conventions for every entry point:
+ *   - device pointers unless the name starts with host_;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default);
+ *   - return value: CBFS_OK (0) or a negative CBFS_E_* status; on error no
+ *     output is partially valid;
+ *   - the graph is undirected: off/adj hold both arc directions.
+ * The library is not thread-safe per handle: calls on one handle must not
+ * overlap in time on the host.
+ */
+#ifndef CBFS_H
+#define CBFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CBFS_OK = 0,
+    CBFS_E_INVALID = -1,  /* bad argument: null pointer, k not in [1,64], d not in
+                             [0,15], source out of range, duplicate source in a cluster */
+    CBFS_E_DIAMETER = -2, /* some vertex saw sources spread more than d rounds apart:
+                             the cluster's diameter exceeds d (Corollary 1 violated) */
+    CBFS_E_DEPTH = -3,    /* some Delta_v would be >= 255 and does not fit one byte
+                             (Section 3.1 stores Delta_v in one byte, D < 256) */
+    CBFS_E_NOMEM = -4,    /* device or pinned host allocation failed, or a request
+                             exceeds the stated memory budget */
+    CBFS_E_TIMEOUT = -5,  /* a bounded device-side wait expired */
+    CBFS_E_CUDA = -6,     /* a CUDA runtime call failed */
+    CBFS_E_GRAPH = -7     /* graph validation failed: offsets not monotone, ids out
+                             of range, self loop, unsorted or duplicate neighbours,
+                             or a missing reverse arc */
+};
+
+typedef struct cbfs_graph_s* cbfs_graph_t;
+typedef struct cbfs_labels_s* cbfs_labels_t;
+
+/* Tuning knobs of the traversal.  Zero fields take the library defaults. */
+typedef struct cbfs_tune_s {
+    /* Direction optimisation (Appendix A, EdgeMap): a round runs dense (pull)
+       when |F| + sum_{u in F} deg(u) > pull_alpha * nnz * (clusters in flight);
+       < 0 disables pull.  0 = default (1/10, the paper's commented rule). */
+    float pull_alpha;
+    /* clusters traversed concurrently in one batched wave (1..16).  0 = default. */
+    int slots;
+    int reserved[6];
+} cbfs_tune_t;
+
+/* Per-cluster work counters of the last traversal on a handle (Theorem 1). */
+typedef struct cbfs_cluster_stats_s {
+    uint64_t frontier_appearances; /* V = sum_i |F_i| */
+    uint64_t arcs_scanned;         /* A = sum_i sum_{u in F_i} deg(u) (push model) */
+    uint64_t reached_arcs;         /* sum of deg(v) over vertices with finite Delta_v */
+    uint64_t rounds;               /* number of non-empty frontiers */
+} cbfs_cluster_stats_t;
+
+/*
+ * Graph residency.  Copies the CSR (off[n+1], adj[nnz]) into device memory
+ * owned by the handle.  off is int64 when off_is_i64 != 0, else int32;
+ * adj is int32 vertex ids.  inputs_on_device selects whether off/adj are
+ * device or host pointers; the caller keeps ownership of them and may free
+ * them when the call returns.  validate != 0 checks the graph (see
+ * CBFS_E_GRAPH) on the device before returning.  The call synchronises
+ * `stream`.  Limits: 0 <= n < 2^31, 0 <= nnz < 2^40.
+ * Problem statement: Section 2 (unweighted graph G = (V, E)).
+ */
+int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t* adj, int64_t nnz,
+                      int inputs_on_device, int validate, void* stream, cbfs_graph_t* out);
+
+/* Frees the handle and everything it owns.  NULL is accepted. */
+int cbfs_graph_destroy(cbfs_graph_t g);
+
+/* n and nnz of the resident graph (host outputs). */
+int cbfs_graph_info(cbfs_graph_t g, int64_t* host_n, int64_t* host_nnz);
+
+/*
+ * One C-BFS (Algorithm 1, Section 3.2) from the k sources host_sources[0..k)
+ * with cluster diameter bound d.  Writes dist[n] and masks[d][n] (device).
+ * Sources must be distinct and in [0, n); 1 <= k <= 64; 0 <= d <= 15.  d must
+ * bound the pairwise source distances, otherwise CBFS_E_DIAMETER is returned
+ * (the library detects the violation rather than producing wrong subsets).
+ * The call returns when the outputs are complete (it synchronises `stream`).
+ * Device scratch is owned by the handle and grown on demand.
+ */
+int cbfs_run(cbfs_graph_t g, const int32_t* host_sources, int k, int d, uint8_t* dist, uint64_t* masks,
+             void* stream);
+
+/*
+ * C clusters with one common diameter bound d: cluster c has the sources
+ * host_sources_concat[host_cluster_off[c] .. host_cluster_off[c+1]).
+ * Outputs dist[C][n], masks[C][d][n].  The clusters are traversed
+ * concurrently, several per wave with per-cluster frontiers sharing each
+ * round's launches (no paper counterpart: the paper runs clusters one after
+ * another, Algorithm "Framework of Landmark Labeling").  tune may be NULL.
+ * Same validation, errors and completion rule as cbfs_run.
+ */
+int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const int32_t* host_cluster_off,
+                     int C, int d, uint8_t* dist, uint64_t* masks, const cbfs_tune_t* tune, void* stream);
+
+/*
+ * Work counters (Theorem 1) of C clusters computed from their outputs
+ * (device dist[C][n], masks[C][d][n], host_ks[C] cluster sizes) on the
+ * resident graph g, written to host_out[C].  Each frontier appearance of
+ * Algorithm 1 is a pair (v, i) with S_v[i] non-empty, so the counters are a
+ * function of the outputs alone.  Synchronises `stream`.  Diagnostic, not on
+ * the traversal path.
+ */
+int cbfs_output_stats(cbfs_graph_t g, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks,
+                      int C, int d, cbfs_cluster_stats_t* host_out, void* stream);
+
+/*
+ * Landmark labels (Section 4.2, Algorithm "Framework of Landmark Labeling"):
+ * a vertex-major store of the cluster distance vectors of up to C_capacity
+ * clusters with common d, in device memory owned by the handle.  The row of
+ * vertex v holds, for every stored cluster c: Delta_v(c) (one byte) and
+ * S_v[0..d-1](c) (64-bit words); row stride = round_up(C_capacity, 8) +
+ * 8 * d * C_capacity bytes.  Fails with CBFS_E_NOMEM when n * stride exceeds
+ * hbm_budget_bytes (0 = no budget) or the allocation fails.
+ */
+int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes, cbfs_labels_t* out);
+int cbfs_labels_destroy(cbfs_labels_t L);
+
+/*
+ * Appends C clusters given in the cluster-major C-BFS output format (device
+ * dist[C][n], masks[C][d][n]) with their sizes host_ks[C] (1..64) into the
+ * vertex-major rows.  CBFS_E_INVALID when the store would exceed C_capacity.
+ * Stream-ordered (asynchronous).
+ */
+int cbfs_labels_append(cbfs_labels_t L, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks,
+                       int C, void* stream);
+
+/* Number of clusters stored so far (host output). */
+int cbfs_labels_count(cbfs_labels_t L, int* host_count);
+
+/* Device pointer to the row store and its stride in bytes (host outputs). */
+int cbfs_labels_rows(cbfs_labels_t L, const uint8_t** host_rows, int64_t* host_stride);
+
+/*
+ * Distance query of the landmark labeling (Section 4.2, "Answering Queries
+ * with Clustered Landmarks"): for each pair (u, v) = (pairs[2t], pairs[2t+1])
+ * (device int32), out[t] (device uint16) = min over stored clusters of
+ * Delta_u + Delta_v + i + j for the smallest i + j with S_u[i] & S_v[j] != 0
+ * (i, j in 0..d, S_d implied), i.e. min over all landmarks s of
+ * delta(u, s) + delta(s, v) -- an upper bound of delta(u, v), exact when a
+ * landmark lies on a shortest u-v path.  u == v gives 0; no common landmark
+ * gives 0xFFFF; a pair with an id outside [0, n) gives 0xFFFF and makes the
+ * next cbfs_labels_status return CBFS_E_INVALID.  Stream-ordered
+ * (asynchronous); q may be 0.
+ */
+int cbfs_query_distance(cbfs_labels_t L, const int32_t* pairs, int64_t q, uint16_t* out, void* stream);
+
+/* Synchronises `stream` and returns (then clears) the label store's device
+ * status word: CBFS_OK or CBFS_E_INVALID after an out-of-range query id. */
+int cbfs_labels_status(cbfs_labels_t L, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* cbfs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBFS_H */

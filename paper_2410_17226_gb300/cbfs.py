@@ -1,0 +1,284 @@
+"""Python binding of libcbfs.so (include/cbfs.h): argument marshalling only.
+
+Every step of the traversal and of the query runs in the CUDA library; this
+module only converts arrays and tensors into pointers and sizes.  PyTorch
+supplies device memory and streams.  There is no CPU fallback: when
+libcbfs.so is missing or CUDA is unavailable, every entry point raises.
+
+Device buffers are torch tensors.  64-bit subset words are stored in
+``torch.int64`` tensors (same bits as the C ABI's uint64_t) and query answers
+in ``torch.int16`` tensors (same bits as uint16_t); ``as_numpy_u64`` /
+``as_numpy_u16`` reinterpret them on the host.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcbfs.so")
+
+OK = 0
+E_INVALID, E_DIAMETER, E_DEPTH, E_NOMEM, E_TIMEOUT, E_CUDA, E_GRAPH = -1, -2, -3, -4, -5, -6, -7
+NO_PATH = 0xFFFF
+UNREACHED = 0xFF
+
+
+class CbfsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().cbfs_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg}")
+        self.code = code
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("pull_alpha", ctypes.c_float), ("slots", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class ClusterStats(ctypes.Structure):
+    _fields_ = [("frontier_appearances", ctypes.c_uint64), ("arcs_scanned", ctypes.c_uint64),
+                ("reached_arcs", ctypes.c_uint64), ("rounds", ctypes.c_uint64)]
+
+
+_lib = None
+
+# name -> (restype, argtypes) for every symbol declared in include/cbfs.h
+_P, _I, _I64, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+SIGNATURES = {
+    "cbfs_graph_create": (_I, [_I64, _P, _I, _P, _I64, _I, _I, _P, _P]),
+    "cbfs_graph_destroy": (_I, [_P]),
+    "cbfs_graph_info": (_I, [_P, _P, _P]),
+    "cbfs_run": (_I, [_P, _P, _I, _I, _P, _P, _P]),
+    "cbfs_run_batched": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "cbfs_output_stats": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
+    "cbfs_labels_create": (_I, [_I64, _I, _I, _SZ, _P]),
+    "cbfs_labels_destroy": (_I, [_P]),
+    "cbfs_labels_append": (_I, [_P, _P, _P, _P, _I, _P]),
+    "cbfs_labels_count": (_I, [_P, _P]),
+    "cbfs_labels_rows": (_I, [_P, _P, _P]),
+    "cbfs_query_distance": (_I, [_P, _P, _I64, _P, _P]),
+    "cbfs_labels_status": (_I, [_P, _P]),
+    "cbfs_status_string": (ctypes.c_char_p, [_I]),
+}
+
+
+def lib():
+    """Loads libcbfs.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise CbfsError(rc, where)
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("the C-BFS library needs a CUDA GPU; there is no CPU path")
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return int(t.data_ptr())
+
+
+def _host_i32(a) -> np.ndarray:
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def as_numpy_u64(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+def as_numpy_u16(t: torch.Tensor) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint16)
+
+
+class Graph:
+    """A CSR graph resident on the GPU (``cbfs_graph_create``).
+
+    ``off``/``adj`` may be NumPy arrays or CPU tensors (copied from host) or
+    CUDA tensors (copied device to device).  ``off`` int64 or int32, ``adj``
+    int32.
+    """
+
+    def __init__(self, off, adj, validate: bool = True, stream=None):
+        _require_cuda()
+        self._h = ctypes.c_void_p()
+        on_dev = isinstance(off, torch.Tensor) and off.is_cuda
+        if on_dev:
+            off_t = off.contiguous()
+            adj_t = adj.to(torch.int32).contiguous()
+            is64 = off_t.dtype == torch.int64
+            if not is64:
+                off_t = off_t.to(torch.int32)
+            n, nnz = off_t.numel() - 1, adj_t.numel()
+            keep = (off_t, adj_t)
+            p_off, p_adj = _ptr(off_t), _ptr(adj_t) if nnz else None
+        else:
+            if isinstance(off, torch.Tensor):
+                off, adj = off.numpy(), adj.numpy()
+            off_a = np.ascontiguousarray(off)
+            is64 = off_a.dtype == np.int64
+            off_a = off_a.astype(np.int64 if is64 else np.int32, copy=False)
+            adj_a = np.ascontiguousarray(adj, dtype=np.int32)
+            n, nnz = off_a.size - 1, adj_a.size
+            keep = (off_a, adj_a)
+            p_off = off_a.ctypes.data
+            p_adj = adj_a.ctypes.data if nnz else None
+        rc = lib().cbfs_graph_create(n, p_off, int(is64), p_adj, nnz, int(on_dev), int(validate),
+                                     _stream_ptr(stream), ctypes.byref(self._h))
+        del keep
+        _check(rc, "cbfs_graph_create")
+        self.n, self.nnz = int(n), int(nnz)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().cbfs_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- traversal -----------------------------------------------------------
+    def run(self, sources, d: int, dist: torch.Tensor | None = None, masks: torch.Tensor | None = None,
+            stream=None):
+        """One C-BFS (``cbfs_run``).  Returns ``(dist uint8[n], masks int64[d, n])``."""
+        S = _host_i32(sources)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dist is None:
+            dist = torch.empty(self.n, dtype=torch.uint8, device=dev)
+        if masks is None:
+            masks = torch.empty((d, self.n), dtype=torch.int64, device=dev)
+        rc = lib().cbfs_run(self._h, S.ctypes.data, int(S.size), int(d), _ptr(dist),
+                            _ptr(masks) if d > 0 else None, _stream_ptr(stream))
+        _check(rc, "cbfs_run")
+        return dist, masks
+
+    def run_batched(self, clusters: Sequence | None, d: int, dist: torch.Tensor | None = None,
+                    masks: torch.Tensor | None = None, tune: dict | None = None, stream=None,
+                    sources_concat=None, cluster_off=None):
+        """C clusters in one call (``cbfs_run_batched``).  ``clusters`` is a list
+        of source arrays; alternatively pass ``sources_concat`` and
+        ``cluster_off`` (the C ABI's layout) with ``clusters=None``.  Returns
+        ``(dist uint8[C, n], masks int64[C, d, n])``."""
+        if clusters is None:
+            src, coff = _host_i32(sources_concat), _host_i32(cluster_off)
+        else:
+            arrs = [_host_i32(c) for c in clusters]
+            coff = np.zeros(len(arrs) + 1, dtype=np.int32)
+            np.cumsum([a.size for a in arrs], out=coff[1:])
+            src = np.concatenate(arrs).astype(np.int32) if arrs else np.zeros(0, np.int32)
+        C = coff.size - 1
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dist is None:
+            dist = torch.empty((C, self.n), dtype=torch.uint8, device=dev)
+        if masks is None:
+            masks = torch.empty((C, d, self.n), dtype=torch.int64, device=dev)
+        t = Tune()
+        if tune:
+            t.pull_alpha = float(tune.get("pull_alpha", 0.0))
+            t.slots = int(tune.get("slots", 0))
+        src_p = src.ctypes.data if src.size else np.zeros(1, np.int32).ctypes.data
+        rc = lib().cbfs_run_batched(self._h, src_p, coff.ctypes.data, int(C), int(d), _ptr(dist),
+                                    _ptr(masks) if d > 0 else None, ctypes.byref(t), _stream_ptr(stream))
+        _check(rc, "cbfs_run_batched")
+        return dist, masks
+
+    def output_stats(self, dist: torch.Tensor, masks: torch.Tensor, ks, d: int, stream=None) -> np.ndarray:
+        """Work counters per cluster (``cbfs_output_stats``): int64 [C, 4] =
+        (frontier appearances V, arcs scanned A, reached arcs, rounds)."""
+        ks = _host_i32(ks)
+        C = ks.size
+        out = (ClusterStats * max(C, 1))()
+        rc = lib().cbfs_output_stats(self._h, _ptr(dist), _ptr(masks) if d > 0 else None, ks.ctypes.data, C, int(d),
+                                     ctypes.cast(out, ctypes.c_void_p), _stream_ptr(stream))
+        _check(rc, "cbfs_output_stats")
+        return np.array([[o.frontier_appearances, o.arcs_scanned, o.reached_arcs, o.rounds] for o in out[:C]],
+                        dtype=np.int64).reshape(C, 4)
+
+
+class Labels:
+    """Vertex-major landmark labels on the GPU and the distance query."""
+
+    def __init__(self, n: int, capacity: int, d: int, budget_bytes: int = 0):
+        _require_cuda()
+        self._h = ctypes.c_void_p()
+        _check(lib().cbfs_labels_create(int(n), int(capacity), int(d), int(budget_bytes), ctypes.byref(self._h)),
+               "cbfs_labels_create")
+        self.n, self.capacity, self.d = int(n), int(capacity), int(d)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().cbfs_labels_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def count(self) -> int:
+        c = ctypes.c_int()
+        _check(lib().cbfs_labels_count(self._h, ctypes.byref(c)), "cbfs_labels_count")
+        return c.value
+
+    def rows(self):
+        """(device pointer, stride in bytes) of the row store."""
+        p, s = ctypes.c_void_p(), ctypes.c_int64()
+        _check(lib().cbfs_labels_rows(self._h, ctypes.byref(p), ctypes.byref(s)), "cbfs_labels_rows")
+        return p.value, s.value
+
+    def append(self, dist: torch.Tensor, masks: torch.Tensor, ks, stream=None):
+        ks = _host_i32(ks)
+        rc = lib().cbfs_labels_append(self._h, _ptr(dist), _ptr(masks) if self.d > 0 else None, ks.ctypes.data,
+                                      int(ks.size), _stream_ptr(stream))
+        _check(rc, "cbfs_labels_append")
+
+    def query(self, pairs: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """pairs: CUDA int32 [q, 2].  Returns int16 [q] holding the uint16 answers."""
+        q = pairs.shape[0] if pairs.dim() == 2 else pairs.numel() // 2
+        if out is None:
+            out = torch.empty(q, dtype=torch.int16, device=pairs.device)
+        rc = lib().cbfs_query_distance(self._h, _ptr(pairs) if q else None, int(q), _ptr(out) if q else None,
+                                       _stream_ptr(stream))
+        _check(rc, "cbfs_query_distance")
+        return out
+
+    def status(self, stream=None) -> int:
+        return int(lib().cbfs_labels_status(self._h, _stream_ptr(stream)))
+
+
+def status_string(code: int) -> str:
+    return lib().cbfs_status_string(int(code)).decode()

@@ -1,0 +1,986 @@
+// libcbfs.so, part 1: graph residency, the Cluster-BFS traversal and its
+// C ABI entry points (include/cbfs.h).
+//
+// The traversal follows Algorithm 1 (Section 3.2) level by level.  Round i
+// has two kernels:
+//
+//   phase A (vertex phase): for every queue entry (cluster slot s, vertex u)
+//     new = acc[u] & ~visit[u]; visit[u] |= new; acc[u] = 0;
+//     Delta_u = i on the first visit;  S_u[i - Delta_u] = new  (stored when
+//     i - Delta_u < d; > d means the cluster diameter exceeds d).
+//     Entries with new sources are compacted per 1024-entry tile with their
+//     arc prefix; lists longer than kBigDeg go to a "big" list cut into
+//     kBigDeg-arc pieces.
+//
+//   phase B (edge phase), one of
+//     push (EdgeMap-Sparse, Appendix A): every frontier arc (u, v) ORs the
+//       new sources of u into acc[v] when they are not already in visit[v]
+//       or acc[v] (checked before the atomic); the pusher that turns acc[v]
+//       from 0 to non-zero appends v to F_{i+1} -- the once-per-round claim
+//       that r[v] implements in Algorithm 1.  Arcs are spread evenly over
+//       the CTAs: big-list pieces first, then tiles whose entries are
+//       located by a binary search of the tile's arc prefix in shared memory.
+//     pull (EdgeMap-Dense): every vertex v whose visit is not ALL ORs the
+//       visit words of all its neighbours (sources at distance <= i from a
+//       neighbour are at distance <= i+1 from v), stops early once ALL is
+//       covered, and keeps the part not in visit[v] as acc[v].  Vertices are
+//       handled by a thread, a warp or a CTA according to their degree.
+//     The direction is chosen per round from |F| + sum deg(F) against
+//     pull_alpha * nnz (the rule of Algorithm "EdgeMap").
+//
+// Readings of the paper (the oracle takes the same ones):
+//   - the sources are seeded into Snext (acc), not Sseen, so round 0 records
+//     S_s[0] = {s};
+//   - new sources are pushed instead of all of Sseen[u]: a source newly set
+//     at v by Sseen[u] must be at distance exactly i from u, so both pushes
+//     set the same bits;
+//   - the edge condition i - Delta_v < d of Algorithm 1 is replaced by the
+//     test new & ~visit[v] & ~acc[v] != 0, which is empty whenever the
+//     condition fails (by Corollary 1 visit[v] = ALL after round Delta_v + d)
+//     and also skips arcs that would not change Snext[v].
+//
+// Several clusters ("slots") are traversed in lockstep: queue entries carry
+// their slot and each slot has its own state and outputs.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "cbfs_internal.cuh"
+
+using namespace cbfs;
+
+namespace {
+
+// ----------------------------------------------------------------- helpers
+
+__device__ __forceinline__ void append(uint64_t* q, unsigned long long* qlen, uint64_t entry) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(qlen, (unsigned long long)__popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    q[base + __popc(mask & ((1u << lane) - 1u))] = entry;
+}
+
+struct ScanSmem {
+    uint32_t a[kWarps];
+    uint32_t b[kWarps];
+};
+
+// Exclusive block-wide scan of two counters (256 threads).
+__device__ __forceinline__ void block_scan2(uint32_t a, uint32_t b, uint32_t& ea, uint32_t& eb, uint32_t& ta,
+                                            uint32_t& tb, ScanSmem& sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t x = __shfl_up_sync(0xffffffffu, ia, o);
+        uint32_t y = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += x; ib += y; }
+    }
+    if (lane == 31) { sm.a[warp] = ia; sm.b[warp] = ib; }
+    __syncthreads();
+    uint32_t pa = 0, pb = 0, sa = 0, sb = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        uint32_t x = sm.a[w], y = sm.b[w];
+        if (w < warp) { pa += x; pb += y; }
+        sa += x; sb += y;
+    }
+    ea = pa + ia - a;
+    eb = pb + ib - b;
+    ta = sa;
+    tb = sb;
+    __syncthreads();
+}
+
+__device__ __forceinline__ uint64_t warp_or(uint64_t x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long x, unsigned long long* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    unsigned long long s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kWarps; ++w) s += red[w];
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+// --------------------------------------------------------------- kernels
+
+// Seeds a wave: acc[S[j]] = bit j and F_0 = S for every slot.
+// seeds[i] = slot << 40 | j << 32 | vertex.
+__global__ void k_seed(Wave w, const uint64_t* seeds, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const uint64_t e = seeds[i];
+        const int s = (int)((e >> 40) & 0xFF), j = (int)((e >> 32) & 0xFF);
+        const uint32_t v = (uint32_t)e;
+        w.slots[s].va[v].y = 1ull << j;
+        w.q0[i] = ((uint64_t)s << 32) | v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.ctl[0].qlen = (unsigned long long)count;
+}
+
+// After a wave: every source must have seen every source of its cluster.
+// Otherwise the cluster is not connected within distance d and the implied
+// last subset S_v[d] would be wrong, so the call fails with CBFS_E_DIAMETER.
+__global__ void k_check_sources(Wave w, const uint64_t* seeds, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const uint64_t e = seeds[i];
+        const int s = (int)((e >> 40) & 0xFF);
+        const uint32_t v = (uint32_t)e;
+        const SlotDesc sd = w.slots[s];
+        if (sd.va[v].x != sd.all) set_status(w.status, CBFS_E_DIAMETER);
+    }
+}
+
+// Phase A: the vertex phase of round `round` and the push work lists.
+__global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
+    __shared__ SlotDesc ss[kMaxSlots];
+    __shared__ ScanSmem scan;
+    __shared__ unsigned long long red[kWarps];
+    __shared__ unsigned int s_active;
+    RoundCtl* c = w.ctl + round;
+    const unsigned long long qlen = c->qlen;
+    if (qlen == 0) return;
+    for (int i = threadIdx.x; i < w.nslots; i += kThreads) ss[i] = w.slots[i];
+    if (threadIdx.x == 0) s_active = 0;
+    __syncthreads();
+    const uint64_t* q = (round & 1) ? w.q1 : w.q0;
+    const unsigned long long ntiles = (qlen + kTile - 1) / kTile;
+    unsigned long long my_nf = 0, my_sdeg = 0;
+    unsigned int my_active = 0;
+    for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        uint32_t keep[kPerThread], dg[kPerThread], sl[kPerThread];
+        int64_t ost[kPerThread];
+        uint64_t fw[kPerThread];
+        uint32_t cnt = 0, arcs = 0;
+#pragma unroll
+        for (int r = 0; r < kPerThread; ++r) {
+            keep[r] = 0;
+            dg[r] = 0;
+            sl[r] = 0;
+            ost[r] = 0;
+            fw[r] = 0;
+            const unsigned long long idx = t * kTile + (unsigned long long)threadIdx.x * kPerThread + r;
+            if (idx >= qlen) continue;
+            const uint64_t e = q[idx];
+            const int s = (int)(e >> 32);
+            const uint32_t u = (uint32_t)e;
+            const SlotDesc& S = ss[s];
+            const ulonglong2 st = S.va[u];
+            const uint64_t nw = st.y & ~st.x;
+            if (st.y) S.va[u] = make_ulonglong2(st.x | nw, 0ull);
+            if (!nw) continue;
+            const int64_t o0 = w.off[u], o1 = w.off[u + 1];
+            const int64_t deg = o1 - o0;
+            const uint8_t dd = S.dist[u];
+            int j;
+            if (dd == 0xFF) {
+                if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
+                else S.dist[u] = (uint8_t)round;
+                j = 0;
+            } else {
+                j = round - (int)dd;
+            }
+            if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = nw;
+            else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
+            my_nf += 1;
+            my_sdeg += (unsigned long long)deg;
+            my_active |= 1u << s;
+            if (deg == 0) continue;
+            if (deg > kBigDeg) {
+                // big list: one entry plus ceil(deg / kBigDeg) piece records
+                const unsigned int bi = atomicAdd(&c->nbig, 1u);
+                BigEntry be;
+                be.ost = o0;
+                be.deg = deg;
+                be.fw = nw;
+                be.slot = s;
+                be.pad = 0;
+                w.big[bi] = be;
+                const unsigned int np = (unsigned int)((deg + kBigDeg - 1) / kBigDeg);
+                const unsigned int p0 = atomicAdd(&c->npieces, np);
+                for (unsigned int p = 0; p < np; ++p) {
+                    w.piece_ent[p0 + p] = bi;
+                    w.piece_no[p0 + p] = p;
+                }
+                continue;
+            }
+            keep[r] = 1;
+            dg[r] = (uint32_t)deg;
+            sl[r] = (uint32_t)s;
+            ost[r] = o0;
+            fw[r] = nw;
+            cnt += 1;
+            arcs += (uint32_t)deg;
+        }
+        uint32_t ecnt, earcs, tcnt, tarcs;
+        block_scan2(cnt, arcs, ecnt, earcs, tcnt, tarcs, scan);
+        const unsigned long long base = t * kTile;
+#pragma unroll
+        for (int r = 0; r < kPerThread; ++r) {
+            if (!keep[r]) continue;
+            const unsigned long long pos = base + ecnt;
+            w.t_pre[pos] = earcs;
+            w.t_ost[pos] = ost[r];
+            w.t_fw[pos] = fw[r];
+            w.t_slot[pos] = (uint8_t)sl[r];
+            ecnt += 1;
+            earcs += dg[r];
+        }
+        if (threadIdx.x == 0) {
+            w.tile_cnt[t] = tcnt;
+            w.tile_arcs[t] = tarcs;
+        }
+    }
+    // per-round totals for the direction decision
+    const unsigned long long bnf = block_sum(my_nf, red);
+    const unsigned long long bsd = block_sum(my_sdeg, red);
+    const unsigned int wa = __reduce_or_sync(0xffffffffu, my_active);
+    if ((threadIdx.x & 31) == 0 && wa) atomicOr(&s_active, wa);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (bnf) atomicAdd(&c->nf, bnf);
+        if (bsd) atomicAdd(&c->sdeg, bsd);
+        if (s_active) atomicOr(&c->slot_active, s_active);
+    }
+}
+
+__device__ __forceinline__ void push_arc(const SlotDesc& S, int s, uint64_t fw, int32_t v, uint64_t* qn,
+                                         unsigned long long* qlen_next) {
+    ulonglong2* p = S.va + v;
+    const ulonglong2 st = *p;  // visit is read-only in phase B; acc only grows, a stale copy is a subset
+    const uint64_t b = fw & ~st.x & ~st.y;
+    bool app = false;
+    if (b) {
+        const unsigned long long old = atomicOr(reinterpret_cast<unsigned long long*>(&p->y), (unsigned long long)b);
+        app = (old == 0ull);
+    }
+    if (app) append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
+}
+
+__device__ __forceinline__ bool decide_pull(const Wave& w, const RoundCtl* c) {
+    if (!(w.alpha > 0.f)) return false;
+    const double work = (double)c->nf + (double)c->sdeg;
+    return work > (double)w.alpha * (double)w.nnz * (double)w.nslots;
+}
+
+// Phase B: the edge phase of round `round`.
+__global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
+    __shared__ SlotDesc ss[kMaxSlots];
+    __shared__ uint32_t spre[kThreads + 1];
+    __shared__ int64_t sost[kThreads];
+    __shared__ uint64_t sfw[kThreads];
+    __shared__ uint8_t sslot[kThreads];
+    __shared__ unsigned int s_work;
+    __shared__ uint64_t sor[kWarps];
+    __shared__ int s_done;
+    RoundCtl* c = w.ctl + round;
+    const unsigned long long qlen = c->qlen;
+    if (qlen == 0) return;
+    for (int i = threadIdx.x; i < w.nslots; i += kThreads) ss[i] = w.slots[i];
+    __syncthreads();
+    uint64_t* qn = (round & 1) ? w.q0 : w.q1;
+    unsigned long long* qlen_next = &w.ctl[round + 1].qlen;
+    const bool pull = decide_pull(w, c);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->mode = pull ? 1 : 0;
+
+    if (!pull) {
+        // big-list pieces: kBigDeg consecutive arcs of one hub per CTA step
+        const unsigned int npieces = c->npieces;
+        for (;;) {
+            if (threadIdx.x == 0) s_work = atomicAdd(&c->piece_ctr, 1u);
+            __syncthreads();
+            const unsigned int p = s_work;
+            __syncthreads();
+            if (p >= npieces) break;
+            const BigEntry be = w.big[w.piece_ent[p]];
+            const int64_t a0 = (int64_t)w.piece_no[p] * kBigDeg;
+            const int64_t a1 = min(be.deg, a0 + kBigDeg);
+            const SlotDesc& S = ss[be.slot];
+            for (int64_t a = a0 + threadIdx.x; a < a1; a += kThreads)
+                push_arc(S, be.slot, be.fw, w.adj[be.ost + a], qn, qlen_next);
+        }
+        // tiles: entries of degree <= kBigDeg, arcs spread over the threads
+        const unsigned long long ntiles = (qlen + kTile - 1) / kTile;
+        for (;;) {
+            if (threadIdx.x == 0) s_work = atomicAdd(&c->tile_ctr, 1u);
+            __syncthreads();
+            const unsigned long long t = s_work;
+            __syncthreads();
+            if (t >= ntiles) break;
+            const uint32_t cnt = w.tile_cnt[t];
+            const uint32_t tarcs = w.tile_arcs[t];
+            const unsigned long long base = t * kTile;
+            for (uint32_t g0 = 0; g0 < cnt; g0 += kThreads) {
+                const uint32_t ge = min((uint32_t)kThreads, cnt - g0);
+                if (threadIdx.x < ge) {
+                    const unsigned long long pos = base + g0 + threadIdx.x;
+                    spre[threadIdx.x] = w.t_pre[pos];
+                    sost[threadIdx.x] = w.t_ost[pos];
+                    sfw[threadIdx.x] = w.t_fw[pos];
+                    sslot[threadIdx.x] = w.t_slot[pos];
+                }
+                if (threadIdx.x == 0) spre[ge] = (g0 + ge < cnt) ? w.t_pre[base + g0 + ge] : tarcs;
+                __syncthreads();
+                const uint32_t a_lo = spre[0], a_hi = spre[ge];
+                for (uint32_t a = a_lo + threadIdx.x; a < a_hi; a += kThreads) {
+                    // last entry e with spre[e] <= a
+                    int lo = 0, hi = (int)ge - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (spre[mid] <= a) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    const int s = sslot[lo];
+                    push_arc(ss[s], s, sfw[lo], w.adj[sost[lo] + (a - spre[lo])], qn, qlen_next);
+                }
+                __syncthreads();
+            }
+        }
+        return;
+    }
+
+    // ---- pull: dense pass over every vertex that can still gain sources
+    const unsigned int active = c->slot_active;
+    // CTA per high-degree vertex
+    for (int64_t i = blockIdx.x; i < w.n_big; i += gridDim.x) {
+        const int32_t v = w.pl_big[i];
+        const int64_t o0 = w.off[v], o1 = w.off[v + 1];
+        for (int s = 0; s < w.nslots; ++s) {
+            if (!((active >> s) & 1u)) continue;
+            const SlotDesc& S = ss[s];
+            const uint64_t vis = S.va[v].x;
+            if (vis == S.all) continue;
+            uint64_t acc = 0;
+            for (int64_t b0 = o0; b0 < o1; b0 += kThreads) {
+                const int64_t e = b0 + threadIdx.x;
+                if (e < o1) acc |= S.va[w.adj[e]].x;
+                const uint64_t wacc = warp_or(acc);
+                if ((threadIdx.x & 31) == 0) sor[threadIdx.x >> 5] = wacc;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    uint64_t x = 0;
+                    for (int k = 0; k < kWarps; ++k) x |= sor[k];
+                    s_done = ((x | vis) == S.all);
+                    sor[0] = x;
+                }
+                __syncthreads();
+                acc = sor[0];
+                const int done = s_done;
+                __syncthreads();
+                if (done) break;
+            }
+            if (threadIdx.x == 0) {
+                const uint64_t nw = acc & ~vis;
+                if (nw) {
+                    S.va[v].y = nw;
+                    append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
+                }
+            }
+        }
+    }
+    // warp per mid-degree vertex
+    {
+        const int lane = threadIdx.x & 31;
+        const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+        const int64_t nw_total = ((int64_t)gridDim.x * kThreads) >> 5;
+        for (int64_t i = gw; i < w.n_mid; i += nw_total) {
+            const int32_t v = w.pl_mid[i];
+            const int64_t o0 = w.off[v], o1 = w.off[v + 1];
+            for (int s = 0; s < w.nslots; ++s) {
+                if (!((active >> s) & 1u)) continue;
+                const SlotDesc& S = ss[s];
+                const uint64_t vis = S.va[v].x;
+                if (vis == S.all) continue;
+                uint64_t acc = 0;
+                for (int64_t b0 = o0; b0 < o1; b0 += 32) {
+                    const int64_t e = b0 + lane;
+                    if (e < o1) acc |= S.va[w.adj[e]].x;
+                    acc = warp_or(acc);
+                    if ((acc | vis) == S.all) break;
+                }
+                if (lane == 0) {
+                    const uint64_t nw = acc & ~vis;
+                    if (nw) {
+                        S.va[v].y = nw;
+                        append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
+                    }
+                }
+            }
+        }
+    }
+    // thread per low-degree vertex
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < w.n_small; i += (int64_t)gridDim.x * kThreads) {
+        const int32_t v = w.pl_small[i];
+        const int64_t o0 = w.off[v], o1 = w.off[v + 1];
+        for (int s = 0; s < w.nslots; ++s) {
+            if (!((active >> s) & 1u)) continue;
+            const SlotDesc& S = ss[s];
+            const uint64_t vis = S.va[v].x;
+            if (vis == S.all) continue;
+            uint64_t acc = 0;
+            for (int64_t e = o0; e < o1; ++e) {
+                acc |= S.va[w.adj[e]].x;
+                if ((acc | vis) == S.all) break;
+            }
+            const uint64_t nw = acc & ~vis;
+            if (nw) {
+                S.va[v].y = nw;
+                append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
+            }
+        }
+    }
+}
+
+// Graph validation: ids in range, no self loop, strictly increasing lists,
+// every arc has its reverse.  flag = 1 on the first failure.
+__global__ void k_validate(int64_t n, const int64_t* off, const int32_t* adj, int* flag) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o0 = off[v], o1 = off[v + 1];
+        int32_t prev = -1;
+        for (int64_t e = o0; e < o1; ++e) {
+            const int32_t u = adj[e];
+            if (u < 0 || (int64_t)u >= n || (int64_t)u == v || u <= prev) { atomicExch(flag, 1); return; }
+            prev = u;
+            int64_t lo = off[u], hi = off[u + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((int64_t)adj[mid] < v) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= off[u + 1] || (int64_t)adj[lo] != v) { atomicExch(flag, 1); return; }
+        }
+    }
+}
+
+// Work counters from outputs: per (cluster, vertex) the number of non-empty
+// subsets among S_v[0..d] (S_v[d] implied).
+__global__ void k_output_stats(int64_t n, int d, const int64_t* off, const uint8_t* dist, const uint64_t* masks,
+                               const uint64_t* alls, int C, unsigned long long* out /*[C][4]*/) {
+    __shared__ unsigned long long red[kWarps];
+    const int c = blockIdx.y;
+    if (c >= C) return;
+    const uint8_t* dc = dist + (size_t)c * (size_t)n;
+    const uint64_t* mc = masks + (size_t)c * (size_t)d * (size_t)n;
+    unsigned long long V = 0, A = 0, R = 0, rounds = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t dd = dc[v];
+        if (dd == 0xFF) continue;
+        const unsigned long long deg = (unsigned long long)(off[v + 1] - off[v]);
+        uint64_t seen = 0;
+        int cnt = 0, last = 0;
+        for (int i = 0; i < d; ++i) {
+            const uint64_t m = mc[(size_t)i * (size_t)n + v];
+            if (m) { cnt++; last = i; }
+            seen |= m;
+        }
+        if (alls[c] & ~seen) { cnt++; last = d; }
+        V += cnt;
+        A += (unsigned long long)cnt * deg;
+        R += deg;
+        const unsigned long long rr = (unsigned long long)dd + (unsigned long long)last + 1;
+        rounds = rr > rounds ? rr : rounds;
+    }
+    const unsigned long long bV = block_sum(V, red);
+    const unsigned long long bA = block_sum(A, red);
+    const unsigned long long bR = block_sum(R, red);
+    unsigned long long m = rounds;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
+        m = x > m ? x : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&out[c * 4 + 3], m);
+    if (threadIdx.x == 0) {
+        atomicAdd(&out[c * 4 + 0], bV);
+        atomicAdd(&out[c * 4 + 1], bA);
+        atomicAdd(&out[c * 4 + 2], bR);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- host side
+
+struct cbfs_graph_s {
+    int64_t n = 0, nnz = 0;
+    int64_t* off = nullptr;
+    int32_t* adj = nullptr;
+    int32_t* pl = nullptr;  // pull lists: small | mid | big
+    int64_t n_small = 0, n_mid = 0, n_big = 0;
+    int64_t big_vertices = 0, big_pieces = 0;
+    int grid = 0;
+    int device = 0;
+    // scratch, sized for cap_slots clusters in flight
+    int cap_slots = 0;
+    ulonglong2* va = nullptr;
+    uint64_t* q0 = nullptr;
+    uint64_t* q1 = nullptr;
+    uint32_t* t_pre = nullptr;
+    int64_t* t_ost = nullptr;
+    uint64_t* t_fw = nullptr;
+    uint8_t* t_slot = nullptr;
+    uint32_t* tile_cnt = nullptr;
+    uint32_t* tile_arcs = nullptr;
+    BigEntry* big = nullptr;
+    uint32_t* piece_ent = nullptr;
+    uint32_t* piece_no = nullptr;
+    RoundCtl* ctl = nullptr;
+    int* status = nullptr;
+    // per-call buffers, grown on demand
+    SlotDesc* slots = nullptr;
+    int64_t slots_cap = 0;
+    uint64_t* seeds = nullptr;
+    int64_t seeds_cap = 0;
+    // pinned host staging
+    unsigned long long* h_q = nullptr;  // [kMaxRounds + 2]
+    SlotDesc* h_slots = nullptr;
+    int64_t h_slots_cap = 0;
+    uint64_t* h_seeds = nullptr;
+    int64_t h_seeds_cap = 0;
+};
+
+namespace {
+
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            g_last_cuda_error = e_;                \
+            return e_ == cudaErrorMemoryAllocation \
+                       ? CBFS_E_NOMEM              \
+                       : CBFS_E_CUDA;              \
+        }                                          \
+    } while (0)
+
+template <class T>
+int dev_alloc(T** p, int64_t count) {
+    *p = nullptr;
+    if (count < 1) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+        g_last_cuda_error = e;
+        cudaGetLastError();
+        *p = nullptr;
+        return CBFS_E_NOMEM;
+    }
+    return CBFS_OK;
+}
+
+template <class T>
+void dev_free(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void free_scratch(cbfs_graph_s* g) {
+    dev_free(g->va);
+    dev_free(g->q0);
+    dev_free(g->q1);
+    dev_free(g->t_pre);
+    dev_free(g->t_ost);
+    dev_free(g->t_fw);
+    dev_free(g->t_slot);
+    dev_free(g->tile_cnt);
+    dev_free(g->tile_arcs);
+    dev_free(g->big);
+    dev_free(g->piece_ent);
+    dev_free(g->piece_no);
+    g->cap_slots = 0;
+}
+
+int ensure_scratch(cbfs_graph_s* g, int P) {
+    if (g->cap_slots >= P) return CBFS_OK;
+    free_scratch(g);
+    const int64_t n = g->n;
+    const int64_t entries = (int64_t)P * n;
+    const int64_t tiles = (entries + kTile - 1) / kTile;
+    int rc = CBFS_OK;
+    if (!rc) rc = dev_alloc(&g->va, entries);
+    if (!rc) rc = dev_alloc(&g->q0, entries);
+    if (!rc) rc = dev_alloc(&g->q1, entries);
+    if (!rc) rc = dev_alloc(&g->t_pre, tiles * kTile);
+    if (!rc) rc = dev_alloc(&g->t_ost, tiles * kTile);
+    if (!rc) rc = dev_alloc(&g->t_fw, tiles * kTile);
+    if (!rc) rc = dev_alloc(&g->t_slot, tiles * kTile);
+    if (!rc) rc = dev_alloc(&g->tile_cnt, tiles);
+    if (!rc) rc = dev_alloc(&g->tile_arcs, tiles);
+    if (!rc) rc = dev_alloc(&g->big, (int64_t)P * g->big_vertices);
+    if (!rc) rc = dev_alloc(&g->piece_ent, (int64_t)P * g->big_pieces);
+    if (!rc) rc = dev_alloc(&g->piece_no, (int64_t)P * g->big_pieces);
+    if (rc) {
+        free_scratch(g);
+        return rc;
+    }
+    g->cap_slots = P;
+    return CBFS_OK;
+}
+
+template <class T>
+int ensure_dev(T** p, int64_t* cap, int64_t want) {
+    if (*cap >= want) return CBFS_OK;
+    dev_free(*p);
+    *cap = 0;
+    int rc = dev_alloc(p, want);
+    if (rc) return rc;
+    *cap = want;
+    return CBFS_OK;
+}
+
+template <class T>
+int ensure_pinned(T** p, int64_t* cap, int64_t want) {
+    if (*cap >= want) return CBFS_OK;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMallocHost((void**)p, sizeof(T) * (size_t)std::max<int64_t>(want, 1));
+    if (e != cudaSuccess) {
+        g_last_cuda_error = e;
+        cudaGetLastError();
+        *p = nullptr;
+        return CBFS_E_NOMEM;
+    }
+    *cap = want;
+    return CBFS_OK;
+}
+
+int check_clusters(const cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C, int d) {
+    if (d < 0 || d > 15) return CBFS_E_INVALID;
+    if (coff[0] != 0) return CBFS_E_INVALID;
+    int32_t buf[64];
+    for (int c = 0; c < C; ++c) {
+        const int64_t k = (int64_t)coff[c + 1] - coff[c];
+        if (k < 1 || k > 64) return CBFS_E_INVALID;
+        for (int64_t j = 0; j < k; ++j) {
+            const int32_t v = src[coff[c] + j];
+            if (v < 0 || (int64_t)v >= g->n) return CBFS_E_INVALID;
+            buf[j] = v;
+        }
+        std::sort(buf, buf + k);
+        for (int64_t j = 1; j < k; ++j)
+            if (buf[j] == buf[j - 1]) return CBFS_E_INVALID;
+    }
+    return CBFS_OK;
+}
+
+int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C, int d, uint8_t* dist,
+                 uint64_t* masks, const cbfs_tune_t* tune, cudaStream_t st) {
+    int rc = check_clusters(g, src, coff, C, d);
+    if (rc) return rc;
+    if (C == 0) return CBFS_OK;
+    CK(cudaSetDevice(g->device));
+    int P = (tune && tune->slots > 0) ? tune->slots : 2;
+    P = std::max(1, std::min(P, std::min(C, kMaxSlots)));
+    float alpha = 0.1f;
+    if (tune && tune->pull_alpha != 0.f) alpha = tune->pull_alpha;
+    rc = ensure_scratch(g, P);
+    if (rc) return rc;
+    const int nwaves = (C + P - 1) / P;
+    const int64_t total_src = coff[C];
+    rc = ensure_dev(&g->slots, &g->slots_cap, (int64_t)nwaves * P);
+    if (!rc) rc = ensure_pinned(&g->h_slots, &g->h_slots_cap, (int64_t)nwaves * P);
+    if (!rc) rc = ensure_dev(&g->seeds, &g->seeds_cap, total_src);
+    if (!rc) rc = ensure_pinned(&g->h_seeds, &g->h_seeds_cap, total_src);
+    if (rc) return rc;
+    // slot tables and seeds of every wave, staged once
+    const int64_t n = g->n;
+    std::vector<int64_t> wave_seed_off(nwaves + 1, 0);
+    int64_t ns = 0;
+    for (int wv = 0; wv < nwaves; ++wv) {
+        wave_seed_off[wv] = ns;
+        for (int s = 0; s < P; ++s) {
+            const int c = wv * P + s;
+            SlotDesc sd;
+            memset(&sd, 0, sizeof(sd));
+            if (c < C) {
+                const int k = coff[c + 1] - coff[c];
+                sd.va = g->va + (size_t)s * (size_t)n;
+                sd.dist = dist + (size_t)c * (size_t)n;
+                sd.masks = d ? masks + (size_t)c * (size_t)d * (size_t)n : nullptr;
+                sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
+                sd.cluster = c;
+                for (int j = 0; j < k; ++j)
+                    g->h_seeds[ns++] = ((uint64_t)s << 40) | ((uint64_t)j << 32) | (uint32_t)src[coff[c] + j];
+            }
+            g->h_slots[(size_t)wv * P + s] = sd;
+        }
+    }
+    wave_seed_off[nwaves] = ns;
+    CK(cudaMemcpyAsync(g->slots, g->h_slots, sizeof(SlotDesc) * (size_t)nwaves * P, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g->seeds, g->h_seeds, sizeof(uint64_t) * (size_t)std::max<int64_t>(ns, 1),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(g->status, 0, sizeof(int), st));
+
+    Wave w;
+    memset(&w, 0, sizeof(w));
+    w.n = n;
+    w.nnz = g->nnz;
+    w.off = g->off;
+    w.adj = g->adj;
+    w.d = d;
+    w.q0 = g->q0;
+    w.q1 = g->q1;
+    w.ctl = g->ctl;
+    w.t_pre = g->t_pre;
+    w.t_ost = g->t_ost;
+    w.t_fw = g->t_fw;
+    w.t_slot = g->t_slot;
+    w.tile_cnt = g->tile_cnt;
+    w.tile_arcs = g->tile_arcs;
+    w.big = g->big;
+    w.piece_ent = g->piece_ent;
+    w.piece_no = g->piece_no;
+    w.pl_small = g->pl;
+    w.pl_mid = g->pl + g->n_small;
+    w.pl_big = g->pl + g->n_small + g->n_mid;
+    w.n_small = g->n_small;
+    w.n_mid = g->n_mid;
+    w.n_big = g->n_big;
+    w.status = g->status;
+    w.alpha = alpha;
+
+    for (int wv = 0; wv < nwaves; ++wv) {
+        const int c0 = wv * P;
+        const int nsl = std::min(P, C - c0);
+        w.nslots = nsl;
+        w.slots = g->slots + (size_t)wv * P;
+        CK(cudaMemsetAsync(g->va, 0, sizeof(ulonglong2) * (size_t)nsl * (size_t)n, st));
+        CK(cudaMemsetAsync(dist + (size_t)c0 * (size_t)n, 0xFF, (size_t)nsl * (size_t)n, st));
+        if (d) CK(cudaMemsetAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, 0, sizeof(uint64_t) * (size_t)nsl * d * n, st));
+        CK(cudaMemsetAsync(g->ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
+        const int cnt = (int)(wave_seed_off[wv + 1] - wave_seed_off[wv]);
+        k_seed<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
+        CK(cudaGetLastError());
+        bool done = false;
+        for (int r = 0; r < kMaxRounds - 1 && !done; ++r) {
+            k_phase_a<<<g->grid, kThreads, 0, st>>>(w, r);
+            k_phase_b<<<g->grid, kThreads, 0, st>>>(w, r);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&g->h_q[r + 1], &g->ctl[r + 1].qlen, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+            if (r % 2 == 1 || r == kMaxRounds - 2) {
+                CK(cudaStreamSynchronize(st));
+                if (g->h_q[r] == 0 || g->h_q[r + 1] == 0) done = true;
+            }
+        }
+        if (!done) {
+            CK(cudaStreamSynchronize(st));
+            return CBFS_E_DEPTH;
+        }
+        k_check_sources<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
+        CK(cudaGetLastError());
+    }
+    int status = 0;
+    CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cbfs_status_string(int status) {
+    switch (status) {
+        case CBFS_OK: return "CBFS_OK";
+        case CBFS_E_INVALID: return "CBFS_E_INVALID: invalid argument";
+        case CBFS_E_DIAMETER: return "CBFS_E_DIAMETER: cluster diameter exceeds d";
+        case CBFS_E_DEPTH: return "CBFS_E_DEPTH: a distance does not fit one byte (>= 255)";
+        case CBFS_E_NOMEM: return "CBFS_E_NOMEM: out of memory or over budget";
+        case CBFS_E_TIMEOUT: return "CBFS_E_TIMEOUT: bounded device wait expired";
+        case CBFS_E_CUDA: return "CBFS_E_CUDA: CUDA runtime error";
+        case CBFS_E_GRAPH: return "CBFS_E_GRAPH: graph validation failed";
+        default: return "CBFS: unknown status";
+    }
+}
+
+int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t* adj, int64_t nnz,
+                      int inputs_on_device, int validate, void* stream, cbfs_graph_t* out) {
+    if (!out) return CBFS_E_INVALID;
+    *out = nullptr;
+    if (n < 0 || n >= (int64_t)0x7fffffff || nnz < 0 || nnz >= ((int64_t)1 << 40)) return CBFS_E_INVALID;
+    if (!off || (nnz > 0 && !adj)) return CBFS_E_INVALID;
+    if (!off_is_i64 && nnz > 0x7fffffffLL) return CBFS_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    // host copy of the offsets (degree classes and capacity planning)
+    std::vector<int64_t> h_off((size_t)n + 1);
+    if (off_is_i64) {
+        if (inputs_on_device) CK(cudaMemcpy(h_off.data(), off, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToHost));
+        else memcpy(h_off.data(), off, sizeof(int64_t) * (size_t)(n + 1));
+    } else {
+        std::vector<int32_t> o32((size_t)n + 1);
+        if (inputs_on_device) CK(cudaMemcpy(o32.data(), off, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyDeviceToHost));
+        else memcpy(o32.data(), off, sizeof(int32_t) * (size_t)(n + 1));
+        for (int64_t v = 0; v <= n; ++v) h_off[v] = o32[v];
+    }
+    if (h_off[0] != 0 || h_off[n] != nnz) return CBFS_E_GRAPH;
+    for (int64_t v = 0; v < n; ++v)
+        if (h_off[v + 1] < h_off[v]) return CBFS_E_GRAPH;
+
+    cbfs_graph_s* g = new (std::nothrow) cbfs_graph_s();
+    if (!g) return CBFS_E_NOMEM;
+    int rc = CBFS_OK;
+    auto fail = [&](int code) {
+        cbfs_graph_destroy(g);
+        return code;
+    };
+    cudaGetDevice(&g->device);
+    g->n = n;
+    g->nnz = nnz;
+    rc = dev_alloc(&g->off, n + 1);
+    if (!rc) rc = dev_alloc(&g->adj, nnz);
+    if (!rc) rc = dev_alloc(&g->ctl, kMaxRounds);
+    if (!rc) rc = dev_alloc(&g->status, 1);
+    if (rc) return fail(rc);
+    if (cudaMallocHost((void**)&g->h_q, sizeof(unsigned long long) * (kMaxRounds + 2)) != cudaSuccess) {
+        g->h_q = nullptr;
+        return fail(CBFS_E_NOMEM);
+    }
+    if (cudaMemcpyAsync(g->off, h_off.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(CBFS_E_CUDA);
+    if (nnz > 0 && cudaMemcpyAsync(g->adj, adj, sizeof(int32_t) * (size_t)nnz,
+                                   inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(CBFS_E_CUDA);
+    // degree classes for pull, capacity of the push big list
+    std::vector<int32_t> ls, lm, lb;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t dg = h_off[v + 1] - h_off[v];
+        if (dg == 0) continue;
+        if (dg <= kPullSmall) ls.push_back((int32_t)v);
+        else if (dg <= kPullMid) lm.push_back((int32_t)v);
+        else lb.push_back((int32_t)v);
+        if (dg > kBigDeg) {
+            g->big_vertices += 1;
+            g->big_pieces += (dg + kBigDeg - 1) / kBigDeg;
+        }
+    }
+    g->n_small = (int64_t)ls.size();
+    g->n_mid = (int64_t)lm.size();
+    g->n_big = (int64_t)lb.size();
+    rc = dev_alloc(&g->pl, g->n_small + g->n_mid + g->n_big);
+    if (rc) return fail(rc);
+    if (g->n_small) cudaMemcpyAsync(g->pl, ls.data(), sizeof(int32_t) * ls.size(), cudaMemcpyHostToDevice, st);
+    if (g->n_mid) cudaMemcpyAsync(g->pl + g->n_small, lm.data(), sizeof(int32_t) * lm.size(), cudaMemcpyHostToDevice, st);
+    if (g->n_big)
+        cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, lb.data(), sizeof(int32_t) * lb.size(), cudaMemcpyHostToDevice, st);
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phase_b, kThreads, 0);
+    g->grid = std::max(1, sms) * std::max(1, std::min(occ, 8));
+    if (validate && n > 0) {
+        if (cudaMemsetAsync(g->status, 0, sizeof(int), st) != cudaSuccess) return fail(CBFS_E_CUDA);
+        k_validate<<<std::max(1, sms) * 4, kThreads, 0, st>>>(n, g->off, g->adj, g->status);
+        int flag = 0;
+        if (cudaMemcpyAsync(&flag, g->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(CBFS_E_CUDA);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);
+        if (flag) return fail(CBFS_E_GRAPH);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);
+    if (cudaGetLastError() != cudaSuccess) return fail(CBFS_E_CUDA);
+    *out = g;
+    return CBFS_OK;
+}
+
+int cbfs_graph_destroy(cbfs_graph_t g) {
+    if (!g) return CBFS_OK;
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    free_scratch(g);
+    dev_free(g->off);
+    dev_free(g->adj);
+    dev_free(g->pl);
+    dev_free(g->ctl);
+    dev_free(g->status);
+    dev_free(g->slots);
+    dev_free(g->seeds);
+    if (g->h_q) cudaFreeHost(g->h_q);
+    if (g->h_slots) cudaFreeHost(g->h_slots);
+    if (g->h_seeds) cudaFreeHost(g->h_seeds);
+    delete g;
+    return CBFS_OK;
+}
+
+int cbfs_graph_info(cbfs_graph_t g, int64_t* host_n, int64_t* host_nnz) {
+    if (!g) return CBFS_E_INVALID;
+    if (host_n) *host_n = g->n;
+    if (host_nnz) *host_nnz = g->nnz;
+    return CBFS_OK;
+}
+
+int cbfs_run(cbfs_graph_t g, const int32_t* host_sources, int k, int d, uint8_t* dist, uint64_t* masks,
+             void* stream) {
+    if (!g || !host_sources || !dist || (d > 0 && !masks)) return CBFS_E_INVALID;
+    if (k < 1 || k > 64) return CBFS_E_INVALID;
+    const int32_t coff[2] = {0, k};
+    cbfs_tune_t t;
+    memset(&t, 0, sizeof(t));
+    t.slots = 1;
+    return run_clusters(g, host_sources, coff, 1, d, dist, masks, &t, (cudaStream_t)stream);
+}
+
+int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const int32_t* host_cluster_off, int C,
+                     int d, uint8_t* dist, uint64_t* masks, const cbfs_tune_t* tune, void* stream) {
+    if (!g || C < 0 || !host_cluster_off) return CBFS_E_INVALID;
+    if (C == 0) return CBFS_OK;
+    if (!host_sources_concat || !dist || (d > 0 && !masks)) return CBFS_E_INVALID;
+    return run_clusters(g, host_sources_concat, host_cluster_off, C, d, dist, masks, tune, (cudaStream_t)stream);
+}
+
+int cbfs_output_stats(cbfs_graph_t g, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks, int C,
+                      int d, cbfs_cluster_stats_t* host_out, void* stream) {
+    if (!g || C < 0 || d < 0 || d > 15 || !host_out || !host_ks) return CBFS_E_INVALID;
+    if (C == 0) return CBFS_OK;
+    if (!dist || (d > 0 && !masks)) return CBFS_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<uint64_t> alls((size_t)C);
+    for (int c = 0; c < C; ++c) {
+        if (host_ks[c] < 1 || host_ks[c] > 64) return CBFS_E_INVALID;
+        alls[c] = host_ks[c] >= 64 ? ~0ull : ((1ull << host_ks[c]) - 1ull);
+    }
+    uint64_t* d_alls = nullptr;
+    unsigned long long* d_out = nullptr;
+    int rc = dev_alloc(&d_alls, C);
+    if (!rc) rc = dev_alloc(&d_out, (int64_t)C * 4);
+    if (rc) {
+        dev_free(d_alls);
+        return rc;
+    }
+    std::vector<unsigned long long> h((size_t)C * 4);
+    cudaError_t e = cudaMemcpyAsync(d_alls, alls.data(), sizeof(uint64_t) * C, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, sizeof(unsigned long long) * C * 4, st);
+    if (e == cudaSuccess) {
+        dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((g->n + kThreads - 1) / kThreads, 1024)), (unsigned)C);
+        k_output_stats<<<grid, kThreads, 0, st>>>(g->n, d, g->off, dist, masks, d_alls, C, d_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d_out, sizeof(unsigned long long) * C * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(d_alls);
+    dev_free(d_out);
+    if (e != cudaSuccess) {
+        g_last_cuda_error = e;
+        return CBFS_E_CUDA;
+    }
+    for (int c = 0; c < C; ++c) {
+        host_out[c].frontier_appearances = h[c * 4 + 0];
+        host_out[c].arcs_scanned = h[c * 4 + 1];
+        host_out[c].reached_arcs = h[c * 4 + 2];
+        host_out[c].rounds = h[c * 4 + 3];
+    }
+    return CBFS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// libcbfs.so, part 2: landmark labels and the distance query (Section 4.2).
+//
+// Label store: one row per vertex v (the L[v][.] of Algorithm "Framework of
+// Landmark Labeling"), holding for every stored cluster c the byte
+// Delta_v(c) and the words S_v[0..d-1](c):
+//   [ dist: Ccap bytes | pad to P = round_up(Ccap, 8) | d blocks of Ccap u64 ]
+// so one query reads two contiguous rows.
+//
+// Query (Section 4.2, "Answering Queries with Clustered Landmarks"): for a
+// cluster, the distance through its best landmark is Delta_u + Delta_v + t
+// for the smallest t = i + j with S_u[i] & S_v[j] != 0 (i, j in 0..d, S_d
+// implied as ALL minus the stored subsets); the answer is the minimum over
+// clusters.  One warp handles one pair, lanes stride over clusters.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "cbfs_internal.cuh"
+
+using namespace cbfs;
+
+struct cbfs_labels_s {
+    int64_t n = 0;
+    int cap = 0;
+    int d = 0;
+    int count = 0;
+    int64_t P = 0;
+    int64_t stride = 0;
+    uint8_t* rows = nullptr;
+    uint64_t* alls = nullptr;  // [cap]
+    int* status = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+constexpr int kTV = 64;  // vertices per transpose tile
+constexpr int kTC = 32;  // clusters per transpose tile
+
+// Cluster-major outputs -> vertex-major rows for clusters [c0, c0 + C).
+__global__ void __launch_bounds__(256) k_labels_append(int64_t n, int d, int C, int c0, int cap, int64_t P,
+                                                       int64_t stride, const uint8_t* dist, const uint64_t* masks,
+                                                       uint8_t* rows) {
+    __shared__ uint64_t tm[kTC][kTV + 1];
+    __shared__ uint8_t td[kTC][kTV + 4];
+    const int64_t v0 = (int64_t)blockIdx.x * kTV;
+    const int cb = blockIdx.y * kTC;
+    const int nc = min(kTC, C - cb);
+    const int nv = (int)((n - v0) < (int64_t)kTV ? (n - v0) : (int64_t)kTV);
+    // distances
+    for (int i = threadIdx.x; i < kTC * kTV; i += blockDim.x) {
+        const int c = i / kTV, vv = i % kTV;
+        if (c < nc && vv < nv) td[c][vv] = dist[(size_t)(cb + c) * (size_t)n + v0 + vv];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTC * kTV; i += blockDim.x) {
+        const int vv = i / kTC, c = i % kTC;
+        if (c < nc && vv < nv) rows[(v0 + vv) * stride + c0 + cb + c] = td[c][vv];
+    }
+    // subsets
+    for (int s = 0; s < d; ++s) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kTC * kTV; i += blockDim.x) {
+            const int c = i / kTV, vv = i % kTV;
+            if (c < nc && vv < nv) tm[c][vv] = masks[((size_t)(cb + c) * (size_t)d + s) * (size_t)n + v0 + vv];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kTC * kTV; i += blockDim.x) {
+            const int vv = i / kTC, c = i % kTC;
+            if (c < nc && vv < nv) {
+                uint64_t* dst = reinterpret_cast<uint64_t*>(rows + (v0 + vv) * stride + P) + (size_t)s * cap + c0 + cb + c;
+                *dst = tm[c][vv];
+            }
+        }
+    }
+}
+
+// Smallest t = i + j with Su[i] & Sv[j] != 0, or -1.
+template <int D>
+__device__ __forceinline__ int best_offset_fixed(const uint64_t* su, const uint64_t* sv) {
+#pragma unroll
+    for (int t = 0; t <= 2 * D; ++t) {
+        uint64_t hit = 0;
+#pragma unroll
+        for (int i = 0; i <= D; ++i) {
+            const int j = t - i;
+            if (j >= 0 && j <= D) hit |= su[i] & sv[j];
+        }
+        if (hit) return t;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int best_offset_any(const uint64_t* su, const uint64_t* sv, int d) {
+    for (int t = 0; t <= 2 * d; ++t) {
+        uint64_t hit = 0;
+        for (int i = max(0, t - d); i <= min(t, d); ++i) hit |= su[i] & sv[t - i];
+        if (hit) return t;
+    }
+    return -1;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int cap, int64_t P, int64_t stride,
+                                               const uint8_t* rows, const uint64_t* alls, const int32_t* pairs,
+                                               int64_t q, uint16_t* out, int* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    constexpr int DM = (D > 0 ? D : 15) + 1;
+    for (int64_t t = warp; t < q; t += nwarps) {
+        const int32_t u = pairs[2 * t], v = pairs[2 * t + 1];
+        if (u < 0 || v < 0 || (int64_t)u >= n || (int64_t)v >= n) {
+            if (lane == 0) {
+                out[t] = 0xFFFF;
+                atomicCAS(status, 0, CBFS_E_INVALID);
+            }
+            continue;
+        }
+        if (u == v) {
+            if (lane == 0) out[t] = 0;
+            continue;
+        }
+        const uint8_t* ru = rows + (int64_t)u * stride;
+        const uint8_t* rv = rows + (int64_t)v * stride;
+        const uint64_t* mu = reinterpret_cast<const uint64_t*>(ru + P);
+        const uint64_t* mv = reinterpret_cast<const uint64_t*>(rv + P);
+        int best = 0x7fffffff;
+        for (int c = lane; c < C; c += 32) {
+            const int du = ru[c], dv = rv[c];
+            if (du == 0xFF || dv == 0xFF) continue;
+            uint64_t su[DM], sv[DM];
+            uint64_t ou = 0, ov = 0;
+            const int dd = D > 0 ? D : d;
+#pragma unroll
+            for (int i = 0; i < DM - 1; ++i) {
+                if (i < dd) {
+                    su[i] = __ldg(mu + (size_t)i * cap + c);
+                    sv[i] = __ldg(mv + (size_t)i * cap + c);
+                    ou |= su[i];
+                    ov |= sv[i];
+                }
+            }
+            const uint64_t all = __ldg(alls + c);
+            su[dd] = all & ~ou;
+            sv[dd] = all & ~ov;
+            const int off = D > 0 ? best_offset_fixed<D>(su, sv) : best_offset_any(su, sv, dd);
+            if (off >= 0) best = min(best, du + dv + off);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) out[t] = best == 0x7fffffff ? (uint16_t)0xFFFF : (uint16_t)min(best, 0xFFFE);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes, cbfs_labels_t* out) {
+    if (!out || n < 0 || n >= (int64_t)0x7fffffff || C_capacity < 1 || d < 0 || d > 15) return CBFS_E_INVALID;
+    *out = nullptr;
+    cbfs_labels_s* L = new (std::nothrow) cbfs_labels_s();
+    if (!L) return CBFS_E_NOMEM;
+    cudaGetDevice(&L->device);
+    L->n = n;
+    L->cap = C_capacity;
+    L->d = d;
+    L->P = ((int64_t)C_capacity + 7) / 8 * 8;
+    L->stride = L->P + 8 * (int64_t)d * C_capacity;
+    const size_t bytes = (size_t)std::max<int64_t>(n, 1) * (size_t)L->stride;
+    if (hbm_budget_bytes && bytes > hbm_budget_bytes) {
+        delete L;
+        return CBFS_E_NOMEM;
+    }
+    if (cudaMalloc((void**)&L->rows, bytes) != cudaSuccess || cudaMalloc((void**)&L->alls, sizeof(uint64_t) * C_capacity) != cudaSuccess ||
+        cudaMalloc((void**)&L->status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cbfs_labels_destroy(L);
+        return CBFS_E_NOMEM;
+    }
+    if (cudaMemset(L->rows, 0, bytes) != cudaSuccess || cudaMemset(L->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cbfs_labels_destroy(L);
+        return CBFS_E_CUDA;
+    }
+    *out = L;
+    return CBFS_OK;
+}
+
+int cbfs_labels_destroy(cbfs_labels_t L) {
+    if (!L) return CBFS_OK;
+    cudaSetDevice(L->device);
+    cudaDeviceSynchronize();
+    if (L->rows) cudaFree(L->rows);
+    if (L->alls) cudaFree(L->alls);
+    if (L->status) cudaFree(L->status);
+    delete L;
+    return CBFS_OK;
+}
+
+int cbfs_labels_append(cbfs_labels_t L, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks, int C,
+                       void* stream) {
+    if (!L || C < 0 || (C > 0 && (!dist || !host_ks || (L->d > 0 && !masks)))) return CBFS_E_INVALID;
+    if (L->count + C > L->cap) return CBFS_E_INVALID;
+    if (C == 0) return CBFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<uint64_t> alls((size_t)C);
+    for (int c = 0; c < C; ++c) {
+        if (host_ks[c] < 1 || host_ks[c] > 64) return CBFS_E_INVALID;
+        alls[c] = host_ks[c] >= 64 ? ~0ull : ((1ull << host_ks[c]) - 1ull);
+    }
+    // synchronous copy of the small table: the host vector dies with the call
+    if (cudaMemcpy(L->alls + L->count, alls.data(), sizeof(uint64_t) * C, cudaMemcpyHostToDevice) != cudaSuccess)
+        return CBFS_E_CUDA;
+    if (L->n > 0) {
+        dim3 grid((unsigned)((L->n + kTV - 1) / kTV), (unsigned)((C + kTC - 1) / kTC));
+        k_labels_append<<<grid, 256, 0, st>>>(L->n, L->d, C, L->count, L->cap, L->P, L->stride, dist, masks, L->rows);
+        if (cudaGetLastError() != cudaSuccess) return CBFS_E_CUDA;
+    }
+    L->count += C;
+    return CBFS_OK;
+}
+
+int cbfs_labels_count(cbfs_labels_t L, int* host_count) {
+    if (!L || !host_count) return CBFS_E_INVALID;
+    *host_count = L->count;
+    return CBFS_OK;
+}
+
+int cbfs_labels_rows(cbfs_labels_t L, const uint8_t** host_rows, int64_t* host_stride) {
+    if (!L) return CBFS_E_INVALID;
+    if (host_rows) *host_rows = L->rows;
+    if (host_stride) *host_stride = L->stride;
+    return CBFS_OK;
+}
+
+int cbfs_query_distance(cbfs_labels_t L, const int32_t* pairs, int64_t q, uint16_t* out, void* stream) {
+    if (!L || q < 0 || (q > 0 && (!pairs || !out))) return CBFS_E_INVALID;
+    if (q == 0) return CBFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t warps_per_block = 8;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((q + warps_per_block - 1) / warps_per_block, 152 * 16));
+    switch (L->d) {
+        case 1:
+            k_query<1><<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, L->count, L->cap, L->P, L->stride, L->rows, L->alls, pairs, q, out, L->status);
+            break;
+        case 2:
+            k_query<2><<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, L->count, L->cap, L->P, L->stride, L->rows, L->alls, pairs, q, out, L->status);
+            break;
+        default:
+            k_query<0><<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, L->count, L->cap, L->P, L->stride, L->rows, L->alls, pairs, q, out, L->status);
+            break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return CBFS_E_CUDA;
+    return CBFS_OK;
+}
+
+int cbfs_labels_status(cbfs_labels_t L, void* stream) {
+    if (!L) return CBFS_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, L->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return CBFS_E_CUDA;
+    if (cudaMemsetAsync(L->status, 0, sizeof(int), st) != cudaSuccess) return CBFS_E_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CBFS_E_CUDA;
+    return h;
+}
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit for
+bit.  C-BFS is exact integer/bitwise work, so every byte of dist and every
+bit of every subset word must match.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2410_17226_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PUSH_ONLY = {"pull_alpha": -1.0}
+PULL_EAGER = {"pull_alpha": 1e-9}
+
+
+@pytest.fixture(scope="module")
+def cb():
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2410_17226_gb300 import cbfs
+
+    return cbfs
+
+
+def check_one(cb, g, off, adj, S, d, tune=None, oracle_fn=O.cbfs_alg1):
+    od, om = oracle_fn(off, adj, S, d)
+    if tune is None:
+        dist, masks = g.run(S, d)
+    else:
+        dist, masks = g.run_batched([S], d, tune=tune)
+        dist, masks = dist[0], masks[0]
+    gd = dist.cpu().numpy()
+    gm = cb.as_numpy_u64(masks)
+    bad = np.flatnonzero(gd != od)
+    assert bad.size == 0, f"dist differs at {bad[:5]}: gpu {gd[bad[:5]]} oracle {od[bad[:5]]}"
+    bad = np.argwhere(gm != om)
+    assert bad.size == 0, f"masks differ at {bad[:5].tolist()}"
+
+
+def random_cluster(off, adj, rng, kmax=64, hops=2):
+    """Sources within `hops` of a random centre; d = 2 * hops bounds them."""
+    n = off.size - 1
+    c = int(rng.integers(n))
+    dist = O.bfs(off, adj, c)
+    reach = np.flatnonzero((dist >= 0) & (dist <= hops))
+    k = int(min(reach.size, rng.integers(1, kmax + 1)))
+    S = rng.choice(reach, size=k, replace=False).astype(np.int32)
+    return S, min(2 * hops, 15)
+
+
+def test_tiny_random_graphs_all_modes(cb):
+    rng = np.random.default_rng(2410)
+    for t in range(150):
+        n = int(rng.integers(1, 300))
+        off, adj = I.erdos_renyi(n, int(rng.integers(0, 4 * n + 1)), seed=77 + t)
+        g = cb.Graph(off, adj)
+        S, d = random_cluster(off, adj, rng, hops=int(rng.integers(0, 3)))
+        if S.size > 1 and d == 0:
+            d = 2
+        for tune in (None, PUSH_ONLY, PULL_EAGER):
+            check_one(cb, g, off, adj, S, d, tune, oracle_fn=O.cbfs_definition)
+        g.close()
+
+
+def test_config1_rmat_scale14_star_clusters(cb):
+    """R-MAT scale 14, edge factor 16, a random vertex plus up to 63 neighbours, d = 2."""
+    off, adj = I.rmat(14)
+    g = cb.Graph(off, adj)
+    clusters, d = I.star_clusters(off, adj, 6, seed=I.MASTER_SEED + 1)
+    for S in clusters:
+        for tune in (None, PUSH_ONLY, PULL_EAGER):
+            check_one(cb, g, off, adj, S, d, tune)
+
+
+def test_general_d_and_ball_clusters(cb):
+    off, adj = I.road_grid(96, seed=5)
+    g = cb.Graph(off, adj)
+    clusters, ds = I.ball_clusters(off, adj, 4, 64, seed=9)
+    for S, d in zip(clusters, ds):
+        for tune in (None, PUSH_ONLY):
+            check_one(cb, g, off, adj, S, d, tune)
+    # larger d on a power-law graph
+    off, adj = I.rmat(12, seed=3)
+    g = cb.Graph(off, adj)
+    rng = np.random.default_rng(1)
+    for hops in (1, 2, 3):
+        S, d = random_cluster(off, adj, rng, hops=hops)
+        check_one(cb, g, off, adj, S, d)
+
+
+def test_batched_equals_single_and_oracle(cb):
+    off, adj = I.rmat(12, seed=21)
+    g = cb.Graph(off, adj)
+    clusters, d = I.star_clusters(off, adj, 19, seed=4, size="uniform")
+    single = [g.run(S, d) for S in clusters]
+    for tune in (None, {"slots": 1}, {"slots": 3}, {"slots": 16}, dict(PUSH_ONLY, slots=4),
+                 dict(PULL_EAGER, slots=5)):
+        bd, bm = g.run_batched(clusters, d, tune=tune)
+        for c, (sd, sm) in enumerate(single):
+            assert torch.equal(bd[c], sd), (tune, c)
+            assert torch.equal(bm[c], sm), (tune, c)
+    for c, S in enumerate(clusters):
+        od, om = O.cbfs_alg1(off, adj, S, d)
+        assert (single[c][0].cpu().numpy() == od).all()
+        assert (cb.as_numpy_u64(single[c][1]) == om).all()
+
+
+def test_hubs_and_big_lists(cb):
+    # a star with 10000 leaves plus a path hanging off it: hub lists go
+    # through the big-list pieces in push and the CTA-per-vertex pull
+    leaves = 10000
+    src = np.concatenate([np.zeros(leaves, np.int64), np.arange(leaves, leaves + 40)])
+    dst = np.concatenate([np.arange(1, leaves + 1), np.arange(leaves + 1, leaves + 41)])
+    n = leaves + 41
+    off, adj = I.from_edges(n, src, dst)
+    g = cb.Graph(off, adj)
+    for S, d in (([0] + list(range(1, 64)), 2), ([5, 0, 7], 2), ([leaves + 20, leaves + 21], 1), ([3], 0)):
+        S = np.array(S, np.int32)
+        for tune in (None, PUSH_ONLY, PULL_EAGER):
+            check_one(cb, g, off, adj, S, d, tune, oracle_fn=O.cbfs_definition)
+
+
+def test_edge_cases(cb):
+    # single vertex, no edges
+    off, adj = I.from_edges(1, [], [])
+    g = cb.Graph(off, adj)
+    check_one(cb, g, off, adj, np.array([0], np.int32), 0)
+    check_one(cb, g, off, adj, np.array([0], np.int32), 3)
+    # isolated source among others, unreachable components
+    off, adj = I.from_edges(10, [1, 2, 5], [2, 3, 6])
+    g = cb.Graph(off, adj)
+    check_one(cb, g, off, adj, np.array([0], np.int32), 0)
+    check_one(cb, g, off, adj, np.array([2, 1, 3], np.int32), 2)
+    # k = 64 exactly (all bits), d = 1 clique
+    src, dst = np.triu_indices(70, 1)
+    off, adj = I.from_edges(70, src, dst)
+    g = cb.Graph(off, adj)
+    check_one(cb, g, off, adj, np.arange(64, dtype=np.int32), 1)
+    # deepest representable distance: 254 on a path
+    off, adj = I.path(255)
+    g = cb.Graph(off, adj)
+    check_one(cb, g, off, adj, np.array([0], np.int32), 0)
+    check_one(cb, g, off, adj, np.array([0, 1, 2], np.int32), 2)
+
+
+def test_error_paths(cb):
+    off, adj = I.path(300)
+    g = cb.Graph(off, adj)
+    with pytest.raises(cb.CbfsError) as e:
+        g.run([0], 0)  # distance 299 does not fit one byte
+    assert e.value.code == cb.E_DEPTH
+    with pytest.raises(cb.CbfsError) as e:
+        g.run([10, 14], 2)  # pairwise distance 4 > d
+    assert e.value.code == cb.E_DIAMETER
+    for bad_S, bad_d in (([], 2), (list(range(65)), 2), ([1, 1], 2), ([-1], 2), ([300], 2), ([1], 16), ([1], -1)):
+        with pytest.raises(cb.CbfsError) as e:
+            g.run(bad_S, bad_d)
+        assert e.value.code == cb.E_INVALID
+    # sources in two components: not a cluster of diameter d
+    off2, adj2 = I.from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5])
+    g2 = cb.Graph(off2, adj2)
+    with pytest.raises(cb.CbfsError) as e:
+        g2.run([0, 3], 5)
+    assert e.value.code == cb.E_DIAMETER
+    # graph validation
+    bad_off = np.array([0, 1, 1], np.int64)
+    bad_adj = np.array([1], np.int32)  # arc 0->1 without 1->0
+    with pytest.raises(cb.CbfsError) as e:
+        cb.Graph(bad_off, bad_adj, validate=True)
+    assert e.value.code == cb.E_GRAPH
+    with pytest.raises(cb.CbfsError) as e:
+        cb.Graph(np.array([0, 2], np.int64), np.array([0, 0], np.int32), validate=True)
+    assert e.value.code == cb.E_GRAPH
+    # the handle stays usable after errors
+    check_one(cb, g, off, adj, np.array([10, 11, 12], np.int32), 2)
+
+
+def test_device_inputs_and_int32_offsets(cb):
+    off, adj = I.rmat(11, seed=8)
+    S = I.star_clusters(off, adj, 1, seed=3)[0][0]
+    g1 = cb.Graph(torch.from_numpy(off).cuda(), torch.from_numpy(adj).cuda())
+    g2 = cb.Graph(off.astype(np.int32), adj)
+    for g in (g1, g2):
+        check_one(cb, g, off, adj, S, 2)
+
+
+def test_output_stats_match_oracle_counters(cb):
+    off, adj = I.rmat(12, seed=13)
+    g = cb.Graph(off, adj)
+    clusters, d = I.star_clusters(off, adj, 5, seed=6, size="uniform")
+    bd, bm = g.run_batched(clusters, d)
+    st = g.output_stats(bd, bm, [len(S) for S in clusters], d)
+    for c, S in enumerate(clusters):
+        _, _, cnt = O.cbfs_alg1(off, adj, S, d, with_counters=True)
+        assert st[c].tolist() == [cnt["V"], cnt["A"], cnt["reached_arcs"], cnt["rounds"]]
