@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Cluster-BFS hot path.
+
+Workload (one step): batched C-BFS of 256 star clusters (1-64 sources each,
+seeded random centres and neighbour subsets, d = 2) on an undirected R-MAT
+scale-22 graph (edge factor 16, a = 0.57, b = c = 0.19), then the vertex-major
+label append of those 256 clusters and one 65,536-pair distance query.
+Inputs are device-resident when the timed region starts; the CSR (0.5 GB)
+and the outputs (18 GB) are far larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(Algorithm 1, sequential C, one cluster per host core) on a bounded sample of
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2410_17226_gb300 import inputs as I  # noqa: E402
+
+METRIC = "C-BFS source-edge GTEPS + HBM roofline fraction; label-query p50/p99 latency"
+WORKLOAD = ("batched C-BFS: undirected R-MAT scale 22 (edge factor 16, a=0.57 b=c=0.19, int32 CSR), "
+            "256 star clusters of 1-64 sources (seeded random centres + random neighbour subsets), d=2, "
+            "autotuned push/pull; + label append + 65,536-pair query")
+ARC_BYTES = 13      # per arc scanned: 4 B neighbour id + 1 B Delta_v check + 8 B subset OR
+VERTEX_BYTES = 41   # per frontier appearance: 8 B offsets + 33 B vertex-phase reads/writes
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cbfs", "reference"], default="cbfs")
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--clusters", type=int, default=256)
+    ap.add_argument("--query-batch", type=int, default=65536)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--latency-requests", type=int, default=200)
+    ap.add_argument("--fixed-tune", default="", help="'alpha,slots' instead of the autotuner (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def rank_seed(rank: int) -> int:
+    """Cluster seed of a rank: weak scaling gives every rank its own 256 clusters."""
+    return I.MASTER_SEED + 1 + 1000 * rank
+
+
+def workload(scale: int, C: int, rank: int):
+    off, adj = I.rmat(scale)
+    clusters, d = I.star_clusters(off, adj, C, seed=rank_seed(rank), size="uniform")
+    return off, adj, clusters, d
+
+
+# ------------------------------------------------------------ CPU oracle leg
+
+_CPU_G = None  # (off, adj) inherited by forked workers
+
+
+def _oracle_one(args):
+    import oracle
+
+    S, d = args
+    off, adj = _CPU_G
+    t0 = time.perf_counter()
+    _, _, cnt = oracle.cbfs_alg1(off, adj, S, d, with_counters=True)
+    return len(S) * cnt["reached_arcs"] // 2, time.perf_counter() - t0
+
+
+def cpu_oracle_sample(off, adj, clusters, d, budget_s: float):
+    """Times the oracle on the host cores (one cluster per worker) until the
+    budget is used; returns (GTEPS, cores, clusters done, wall seconds)."""
+    global _CPU_G
+    import oracle
+
+    oracle.build()
+    _CPU_G = (off, adj)
+    cores = len(os.sched_getaffinity(0))
+    workers = max(1, min(cores, 64))
+    ctx = mp.get_context("fork")  # forked before any CUDA call in this process
+    done, edges, t0 = 0, 0, time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        while done < len(clusters) and time.perf_counter() - t0 < budget_s:
+            batch = [(clusters[i], d) for i in range(done, min(len(clusters), done + workers))]
+            for e, _ in pool.map(_oracle_one, batch, chunksize=1):
+                edges += e
+            done += len(batch)
+    wall = time.perf_counter() - t0
+    _CPU_G = None
+    return edges / wall / 1e9, workers, done, wall
+
+
+# ------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2410_17226_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernels changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- arms
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    off, adj, clusters, d = workload(args.scale, args.clusters, 0)
+    per_step = []
+    edges_total, wall_total = 0, 0.0
+    cores = 0
+    for k in range(args.warmup + args.steps):
+        sample = clusters[(k * 16) % len(clusters):][:16]
+        g, cores, done, wall = cpu_oracle_sample(off, adj, sample, d, budget_s=args.cpu_budget_s)
+        if k >= args.warmup:
+            per_step.append(wall)
+            edges_total += g * wall * 1e9
+            wall_total += wall
+    value = edges_total / wall_total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall_total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph": f"rmat-s{args.scale}-ef16", "clusters": args.clusters, "d": d},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                         "sample": "each step: 16 of the 256 clusters, Algorithm 1 in plain C, one cluster per core"},
+        "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cbfs(args, ws, rank, local):
+    off, adj, clusters, d = workload(args.scale, args.clusters, rank)
+    C = len(clusters)
+    ks = np.array([len(S) for S in clusters], dtype=np.int32)
+    pairs = I.random_pairs(off.size - 1, args.query_batch, seed=rank_seed(rank) + 7)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        g_cpu, cores, done, wall = cpu_oracle_sample(off, adj, clusters, d, budget_s=args.cpu_budget_s)
+        cpu = {"value": round(g_cpu, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+               "sample": f"{done} of the {C} clusters ({wall:.1f} s wall), Algorithm 1 in plain C, "
+                         f"one cluster per host core"}
+
+    import torch
+
+    from paper_2410_17226_gb300 import build as B
+    from paper_2410_17226_gb300 import cbfs, tune
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist_
+
+        dist_.init_process_group("nccl")
+        pg = dist_
+
+    def barrier():
+        if pg:
+            pg.barrier()
+
+    n = off.size - 1
+    g = cbfs.Graph(off, adj, validate=True)
+    if args.fixed_tune:
+        a_, s_ = args.fixed_tune.split(",")
+        tn = {"pull_alpha": float(a_), "slots": int(s_), "cached": None}
+    else:
+        tn = tune.autotune(g, clusters, d, key_extra=f"rmat-s{args.scale}-{tune.signature(off)}")
+    tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"]}
+    dist = torch.empty((C, n), dtype=torch.uint8, device=dev)
+    masks = torch.empty((C, d, n), dtype=torch.int64, device=dev)
+    L = cbfs.Labels(n, C, d)
+    pairs_dev = torch.from_numpy(pairs).to(dev)
+    answers = torch.empty(args.query_batch, dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream()
+
+    src_cat = np.concatenate(clusters).astype(np.int32)
+    coff = np.concatenate([[0], np.cumsum(ks)]).astype(np.int32)
+
+    def step(ev=None):
+        g.run_batched(None, d, dist, masks, tune=tset, sources_concat=src_cat, cluster_off=coff)
+        if ev is not None:
+            ev.record(stream)
+        L.reset()
+        L.append(dist, masks, ks)
+        L.query(pairs_dev, out=answers)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.profile(True)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t_start.record(stream)
+        for k in range(args.steps):
+            marks[k][0].record(stream)
+            step(marks[k][1])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    prof = g.profile(False)
+    t_ms = t_start.elapsed_time(t_end)
+    cbfs_ms = sum(a.elapsed_time(b) for a, b in marks)
+    t_max = t_ms
+    if pg:
+        tt = torch.tensor([t_ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    st = g.output_stats(dist, masks, ks, d)
+    V, A, R = int(st[:, 0].sum()), int(st[:, 1].sum()), st[:, 2]
+    src_edges = int(sum(int(k) * int(r) // 2 for k, r in zip(ks, R)))
+    units = src_edges * args.steps * ws
+    value = units / (t_max / 1e3) / 1e9
+    alg_bytes_step = ARC_BYTES * A + VERTEX_BYTES * V + C * n * (1 + 8 * d)
+    peak, peak_kind = measured_peak_hbm()
+    e_launch = prof["edge_phase"]["launches"]
+    e_ms = prof["edge_phase"]["ms"]
+    achieved = (ARC_BYTES * A * args.steps) / (e_ms / 1e3) / 1e9 if e_ms > 0 else None
+    traffic = ncu_traffic("k_phase_b")
+    roofline = {"kernel": "k_phase_b (edge phase, push/pull)", "bound": "hbm",
+                "achieved": round(achieved, 1) if achieved else None, "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
+                "peak_kind": peak_kind, "avg_launch_ms": round(e_ms / max(e_launch, 1), 4),
+                "alg_bytes_per_launch": int(ARC_BYTES * A * args.steps / max(e_launch, 1))}
+
+    # label-query latency: single requests of U{1..65536} pairs, H2D + kernel + D2H each
+    lat = []
+    rng = np.random.default_rng(rank_seed(rank) + 11)
+    pin_pairs = torch.from_numpy(pairs).pin_memory()
+    pin_ans = torch.empty(args.query_batch, dtype=torch.int16).pin_memory()
+    qtot, t_q0 = 0, time.perf_counter()
+    for _ in range(args.latency_requests):
+        q = int(rng.integers(1, args.query_batch + 1))
+        t0 = time.perf_counter()
+        pairs_dev[:q].copy_(pin_pairs[:q], non_blocking=True)
+        L.query(pairs_dev[:q], out=answers[:q])
+        pin_ans[:q].copy_(answers[:q], non_blocking=True)
+        torch.cuda.synchronize()
+        lat.append((time.perf_counter() - t0) * 1e3)
+        qtot += q
+    q_wall = time.perf_counter() - t_q0
+    query = {"p50_ms": round(float(np.percentile(lat, 50)), 4), "p99_ms": round(float(np.percentile(lat, 99)), 4),
+             "qps": round(qtot / q_wall, 1), "requests": len(lat), "clusters": C,
+             "mode": "one request at a time, sizes U{1..65536}, pinned H2D + kernel + D2H"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        off_pin = torch.from_numpy(off).pin_memory()
+        adj_pin = torch.from_numpy(adj).pin_memory()
+        dist_h = torch.empty((C, n), dtype=torch.uint8).pin_memory()
+        masks_h = torch.empty((C, d, n), dtype=torch.int64).pin_memory()
+        bi = off.nbytes + adj.nbytes + src_cat.nbytes + coff.nbytes + pairs.nbytes
+        bo = dist_h.numel() + masks_h.numel() * 8 + args.query_batch * 2
+        del dist, masks
+        torch.cuda.empty_cache()
+        e_times = []
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = cbfs.Graph(off_pin, adj_pin, validate=True)
+            dd, mm = g2.run_batched(None, d, tune=tset, sources_concat=src_cat, cluster_off=coff)
+            L.reset()
+            L.append(dd, mm, ks)
+            pairs_dev.copy_(pin_pairs, non_blocking=True)
+            L.query(pairs_dev, out=answers)
+            dist_h.copy_(dd, non_blocking=True)
+            masks_h.copy_(mm, non_blocking=True)
+            pin_ans.copy_(answers, non_blocking=True)
+            torch.cuda.synchronize()
+            e_times.append(time.perf_counter() - t0)
+            g2.close()
+            del dd, mm
+        e_t = max(statistics.median(e_times), 1e-9)
+        e2e = {"value": round(src_edges / e_t / 1e9 * ws, 4), "unit": "GTEPS", "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo), "ms_per_step": round(e_t * 1e3, 3),
+               "includes": "graph create+validate from pinned host CSR, batched C-BFS, label append, query, "
+                           "D2H of dist/masks/answers"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graph": f"rmat-s{args.scale}-ef16", "n": n, "nnz": int(adj.size),
+                       "clusters": C, "sources": int(ks.sum()), "d": d, "tune": tset,
+                       "tune_cached": tn.get("cached"), "query_batch": args.query_batch,
+                       "l2": "inputs larger than L2 (0.5 GB CSR, 18 GB outputs, 18 GB labels)"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(prof["total_launches"] + 2 * args.steps),
+            "clocks": clocks.summary(),
+            "phase_ms_per_step": {"cbfs": round(cbfs_ms / args.steps, 3),
+                                  "labels_query": round((t_ms - cbfs_ms) / args.steps, 3)},
+            "alg_gbs_step": round(alg_bytes_step * args.steps / (t_ms / 1e3) / 1e9, 1),
+            "work_per_step": {"V": V, "A": A, "source_edges": src_edges, "alg_bytes": int(alg_bytes_step)},
+            "kernel_ms": {k: prof[k] for k in ("setup", "vertex_phase", "edge_phase")},
+            "query": query,
+        }
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_cbfs(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

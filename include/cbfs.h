@@ -71,7 +71,7 @@ typedef struct cbfs_tune_s {
     int reserved[6];
 } cbfs_tune_t;
 
-/* Per-cluster work counters of the last traversal on a handle (Theorem 1). */
+/* Work counters of one cluster's traversal (Theorem 1). */
 typedef struct cbfs_cluster_stats_s {
     uint64_t frontier_appearances; /* V = sum_i |F_i| */
     uint64_t arcs_scanned;         /* A = sum_i sum_{u in F_i} deg(u) (push model) */
@@ -133,6 +133,24 @@ int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const i
 int cbfs_output_stats(cbfs_graph_t g, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks,
                       int C, int d, cbfs_cluster_stats_t* host_out, void* stream);
 
+/* Device-time accounting of the traversal kernels of one handle. */
+typedef struct cbfs_kernel_times_s {
+    /* index 0: wave set-up (seed + source check), 1: vertex phase (phase A),
+       2: edge phase (phase B, push or pull) */
+    uint64_t launches[3];
+    double ms[3]; /* summed CUDA-event durations, milliseconds */
+    uint64_t total_launches; /* every kernel the traversal launched */
+} cbfs_kernel_times_t;
+
+/*
+ * enable != 0 makes later cbfs_run / cbfs_run_batched calls on g bracket each
+ * traversal kernel with CUDA events on the call's stream and accumulate the
+ * durations; enable == 0 stops that.  host_out (may be NULL) receives the
+ * totals accumulated since the previous cbfs_profile call, which resets them.
+ * Kernel launch counts are kept even when timing is disabled.
+ */
+int cbfs_profile(cbfs_graph_t g, int enable, cbfs_kernel_times_t* host_out);
+
 /*
  * Landmark labels (Section 4.2, Algorithm "Framework of Landmark Labeling"):
  * a vertex-major store of the cluster distance vectors of up to C_capacity
@@ -153,6 +171,10 @@ int cbfs_labels_destroy(cbfs_labels_t L);
  */
 int cbfs_labels_append(cbfs_labels_t L, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks,
                        int C, void* stream);
+
+/* Forgets every stored cluster (count = 0); the memory stays allocated and
+ * later appends overwrite the rows.  Host-side only, no device work. */
+int cbfs_labels_reset(cbfs_labels_t L);
 
 /* Number of clusters stored so far (host output). */
 int cbfs_labels_count(cbfs_labels_t L, int* host_count);

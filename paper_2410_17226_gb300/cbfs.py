@@ -39,6 +39,13 @@ class Tune(ctypes.Structure):
     _fields_ = [("pull_alpha", ctypes.c_float), ("slots", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64 * 3), ("ms", ctypes.c_double * 3), ("total_launches", ctypes.c_uint64)]
+
+
+KERNEL_KINDS = ("setup", "vertex_phase", "edge_phase")
+
+
 class ClusterStats(ctypes.Structure):
     _fields_ = [("frontier_appearances", ctypes.c_uint64), ("arcs_scanned", ctypes.c_uint64),
                 ("reached_arcs", ctypes.c_uint64), ("rounds", ctypes.c_uint64)]
@@ -55,9 +62,11 @@ SIGNATURES = {
     "cbfs_run": (_I, [_P, _P, _I, _I, _P, _P, _P]),
     "cbfs_run_batched": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
     "cbfs_output_stats": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
+    "cbfs_profile": (_I, [_P, _I, _P]),
     "cbfs_labels_create": (_I, [_I64, _I, _I, _SZ, _P]),
     "cbfs_labels_destroy": (_I, [_P]),
     "cbfs_labels_append": (_I, [_P, _P, _P, _P, _I, _P]),
+    "cbfs_labels_reset": (_I, [_P]),
     "cbfs_labels_count": (_I, [_P, _P]),
     "cbfs_labels_rows": (_I, [_P, _P, _P]),
     "cbfs_query_distance": (_I, [_P, _P, _I64, _P, _P]),
@@ -178,7 +187,7 @@ class Graph:
         if dist is None:
             dist = torch.empty(self.n, dtype=torch.uint8, device=dev)
         if masks is None:
-            masks = torch.empty((d, self.n), dtype=torch.int64, device=dev)
+            masks = torch.empty((max(d, 0), self.n), dtype=torch.int64, device=dev)
         rc = lib().cbfs_run(self._h, S.ctypes.data, int(S.size), int(d), _ptr(dist),
                             _ptr(masks) if d > 0 else None, _stream_ptr(stream))
         _check(rc, "cbfs_run")
@@ -203,7 +212,7 @@ class Graph:
         if dist is None:
             dist = torch.empty((C, self.n), dtype=torch.uint8, device=dev)
         if masks is None:
-            masks = torch.empty((C, d, self.n), dtype=torch.int64, device=dev)
+            masks = torch.empty((C, max(d, 0), self.n), dtype=torch.int64, device=dev)
         t = Tune()
         if tune:
             t.pull_alpha = float(tune.get("pull_alpha", 0.0))
@@ -213,6 +222,15 @@ class Graph:
                                     _ptr(masks) if d > 0 else None, ctypes.byref(t), _stream_ptr(stream))
         _check(rc, "cbfs_run_batched")
         return dist, masks
+
+    def profile(self, enable: bool) -> dict:
+        """Reads and resets the kernel accounting (``cbfs_profile``); ``enable``
+        switches CUDA-event timing of each traversal kernel on or off."""
+        kt = KernelTimes()
+        _check(lib().cbfs_profile(self._h, int(enable), ctypes.byref(kt)), "cbfs_profile")
+        out = {k: {"launches": int(kt.launches[i]), "ms": float(kt.ms[i])} for i, k in enumerate(KERNEL_KINDS)}
+        out["total_launches"] = int(kt.total_launches)
+        return out
 
     def output_stats(self, dist: torch.Tensor, masks: torch.Tensor, ks, d: int, stream=None) -> np.ndarray:
         """Work counters per cluster (``cbfs_output_stats``): int64 [C, 4] =
@@ -247,6 +265,10 @@ class Labels:
             self.close()
         except Exception:
             pass
+
+    def reset(self):
+        """Forgets the stored clusters (``cbfs_labels_reset``); memory is kept."""
+        _check(lib().cbfs_labels_reset(self._h), "cbfs_labels_reset")
 
     @property
     def count(self) -> int:

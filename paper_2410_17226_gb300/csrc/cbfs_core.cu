@@ -550,6 +550,14 @@ struct cbfs_graph_s {
     int64_t h_slots_cap = 0;
     uint64_t* h_seeds = nullptr;
     int64_t h_seeds_cap = 0;
+    // kernel accounting (cbfs_profile)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // pool, reused every call
+    std::vector<int> event_kind;      // kind of the launch bracketed by events [2i, 2i+1]
+    int events_used = 0;
+    uint64_t launches[3] = {0, 0, 0};
+    double ms[3] = {0, 0, 0};
+    uint64_t total_launches = 0;
 };
 
 namespace {
@@ -658,6 +666,39 @@ int ensure_pinned(T** p, int64_t* cap, int64_t want) {
     return CBFS_OK;
 }
 
+// Opens the event bracket of one launch of the given kind when timing.
+int prof_begin(cbfs_graph_s* g, int kind, cudaStream_t st) {
+    g->launches[kind] += 1;
+    g->total_launches += 1;
+    if (!g->timing) return -1;
+    const int i = g->events_used;
+    if ((int)g->events.size() < 2 * (i + 1)) {
+        for (int j = 0; j < 2; ++j) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            g->events.push_back(e);
+        }
+        g->event_kind.push_back(kind);
+    }
+    g->event_kind[i] = kind;
+    g->events_used = i + 1;
+    cudaEventRecord(g->events[2 * i], st);
+    return i;
+}
+
+void prof_end(cbfs_graph_s* g, int slot, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(g->events[2 * slot + 1], st);
+}
+
+// Folds the finished brackets into the totals (the stream has been synchronised).
+void prof_collect(cbfs_graph_s* g) {
+    for (int i = 0; i < g->events_used; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, g->events[2 * i], g->events[2 * i + 1]) == cudaSuccess) g->ms[g->event_kind[i]] += t;
+    }
+    g->events_used = 0;
+}
+
 int check_clusters(const cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C, int d) {
     if (d < 0 || d > 15) return CBFS_E_INVALID;
     if (coff[0] != 0) return CBFS_E_INVALID;
@@ -763,12 +804,18 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
         if (d) CK(cudaMemsetAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, 0, sizeof(uint64_t) * (size_t)nsl * d * n, st));
         CK(cudaMemsetAsync(g->ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
         const int cnt = (int)(wave_seed_off[wv + 1] - wave_seed_off[wv]);
+        int ev = prof_begin(g, 0, st);
         k_seed<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
+        prof_end(g, ev, st);
         CK(cudaGetLastError());
         bool done = false;
         for (int r = 0; r < kMaxRounds - 1 && !done; ++r) {
+            ev = prof_begin(g, 1, st);
             k_phase_a<<<g->grid, kThreads, 0, st>>>(w, r);
+            prof_end(g, ev, st);
+            ev = prof_begin(g, 2, st);
             k_phase_b<<<g->grid, kThreads, 0, st>>>(w, r);
+            prof_end(g, ev, st);
             CK(cudaGetLastError());
             CK(cudaMemcpyAsync(&g->h_q[r + 1], &g->ctl[r + 1].qlen, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
             if (r % 2 == 1 || r == kMaxRounds - 2) {
@@ -778,14 +825,18 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
         }
         if (!done) {
             CK(cudaStreamSynchronize(st));
+            prof_collect(g);
             return CBFS_E_DEPTH;
         }
+        ev = prof_begin(g, 0, st);
         k_check_sources<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
+        prof_end(g, ev, st);
         CK(cudaGetLastError());
     }
     int status = 0;
     CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    prof_collect(g);
     return status;
 }
 
@@ -906,6 +957,7 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->status);
     dev_free(g->slots);
     dev_free(g->seeds);
+    for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     if (g->h_q) cudaFreeHost(g->h_q);
     if (g->h_slots) cudaFreeHost(g->h_slots);
     if (g->h_seeds) cudaFreeHost(g->h_seeds);
@@ -937,6 +989,24 @@ int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const i
     if (C == 0) return CBFS_OK;
     if (!host_sources_concat || !dist || (d > 0 && !masks)) return CBFS_E_INVALID;
     return run_clusters(g, host_sources_concat, host_cluster_off, C, d, dist, masks, tune, (cudaStream_t)stream);
+}
+
+int cbfs_profile(cbfs_graph_t g, int enable, cbfs_kernel_times_t* host_out) {
+    if (!g) return CBFS_E_INVALID;
+    if (host_out) {
+        for (int i = 0; i < 3; ++i) {
+            host_out->launches[i] = g->launches[i];
+            host_out->ms[i] = g->ms[i];
+        }
+        host_out->total_launches = g->total_launches;
+    }
+    for (int i = 0; i < 3; ++i) {
+        g->launches[i] = 0;
+        g->ms[i] = 0.0;
+    }
+    g->total_launches = 0;
+    g->timing = enable != 0;
+    return CBFS_OK;
 }
 
 int cbfs_output_stats(cbfs_graph_t g, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks, int C,

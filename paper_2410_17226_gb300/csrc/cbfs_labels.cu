@@ -222,6 +222,12 @@ int cbfs_labels_append(cbfs_labels_t L, const uint8_t* dist, const uint64_t* mas
     return CBFS_OK;
 }
 
+int cbfs_labels_reset(cbfs_labels_t L) {
+    if (!L) return CBFS_E_INVALID;
+    L->count = 0;
+    return CBFS_OK;
+}
+
 int cbfs_labels_count(cbfs_labels_t L, int* host_count) {
     if (!L || !host_count) return CBFS_E_INVALID;
     *host_count = L->count;

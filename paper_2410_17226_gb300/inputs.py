@@ -33,7 +33,8 @@ returned beside it):
   highest-degree unmarked vertex plus its k-1 highest-degree unmarked
   neighbours, repeated (d = 2).
 * ``ball_clusters``: a random centre plus the next k-1 vertices in BFS order
-  from it; d = twice the BFS level of the last one taken.
+  from it; d = the exact diameter of that set (at most twice the BFS level
+  of the last one taken).
 """
 from __future__ import annotations
 
@@ -250,14 +251,32 @@ def degree_clusters(off, adj, count: int, k: int = 64):
     return out, 2
 
 
-def ball_clusters(off, adj, count: int, k: int, seed: int, max_tries: int = 1000):
+def _bounded_bfs(off, adj, src: int, limit: int) -> dict:
+    """Hop counts from src to every vertex within `limit` hops."""
+    level = {src: 0}
+    frontier = [src]
+    for h in range(1, limit + 1):
+        nxt = []
+        for u in frontier:
+            for v in adj[off[u]:off[u + 1]]:
+                v = int(v)
+                if v not in level:
+                    level[v] = h
+                    nxt.append(v)
+        frontier = nxt
+        if not frontier:
+            break
+    return level
+
+
+def ball_clusters(off, adj, count: int, k: int, seed: int, dmax: int = 15, max_tries: int = 1000):
     """Clusters of a random centre plus the next k-1 vertices in BFS order
     (neighbours taken in adjacency order, i.e. smaller id first).
 
-    Returns ``(list of int32 arrays, list of d)`` where d = 2 * (BFS level of
-    the last vertex taken): every member is within that level of the centre,
-    so every pair is within twice it.  Centres whose component holds fewer
-    than k vertices are redrawn.
+    Returns ``(list of int32 arrays, list of d)`` where d is the exact
+    diameter of the cluster (largest pairwise hop count, found by BFSs bounded
+    at twice the ball radius).  Centres whose component holds fewer than k
+    vertices, or whose cluster diameter exceeds ``dmax``, are redrawn.
     """
     off = np.asarray(off, dtype=np.int64)
     n = off.size - 1
@@ -284,8 +303,16 @@ def ball_clusters(off, adj, count: int, k: int, seed: int, max_tries: int = 1000
                         break
         if len(taken) < k:
             continue
+        radius = level[taken[-1]]
+        members = set(taken)
+        diam = 0
+        for s in taken:
+            lv = _bounded_bfs(off, adj, s, 2 * radius)
+            diam = max(diam, max(lv[t] for t in members))
+        if diam > dmax:
+            continue
         clusters.append(np.asarray(taken, dtype=np.int32))
-        ds.append(2 * level[taken[-1]])
+        ds.append(int(diam))
     return clusters, ds
 
 

@@ -152,8 +152,10 @@ def test_error_paths(cb):
     with pytest.raises(cb.CbfsError) as e:
         g.run([0], 0)  # distance 299 does not fit one byte
     assert e.value.code == cb.E_DEPTH
+    offs, adjs = I.path(50)
+    gs = cb.Graph(offs, adjs)
     with pytest.raises(cb.CbfsError) as e:
-        g.run([10, 14], 2)  # pairwise distance 4 > d
+        gs.run([10, 14], 2)  # pairwise distance 4 > d
     assert e.value.code == cb.E_DIAMETER
     for bad_S, bad_d in (([], 2), (list(range(65)), 2), ([1, 1], 2), ([-1], 2), ([300], 2), ([1], 16), ([1], -1)):
         with pytest.raises(cb.CbfsError) as e:
@@ -174,8 +176,8 @@ def test_error_paths(cb):
     with pytest.raises(cb.CbfsError) as e:
         cb.Graph(np.array([0, 2], np.int64), np.array([0, 0], np.int32), validate=True)
     assert e.value.code == cb.E_GRAPH
-    # the handle stays usable after errors
-    check_one(cb, g, off, adj, np.array([10, 11, 12], np.int32), 2)
+    # the handles stay usable after errors
+    check_one(cb, gs, offs, adjs, np.array([10, 11, 12], np.int32), 2)
 
 
 def test_device_inputs_and_int32_offsets(cb):

@@ -44,7 +44,7 @@ def test_label_rows_match_oracle_layout(cb, chunks):
     n = g.n
 
     class _Rows:  # wraps the device row store for torch, no copy
-        __cuda_array_interface__ = {"shape": (n, stride), "typestr": "|u1", "data": (ptr, True), "version": 3}
+        __cuda_array_interface__ = {"shape": (n, stride), "typestr": "|u1", "data": (ptr, False), "version": 3}
 
     rows = torch.as_tensor(_Rows(), device="cuda").cpu().numpy()
     # oracle layout for capacity 40: pad the cluster axis to the capacity
