@@ -123,6 +123,31 @@ int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const i
                      int C, int d, uint8_t* dist, uint64_t* masks, const cbfs_tune_t* tune, void* stream);
 
 /*
+ * cbfs_run without any allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- a process
+ * whose GPU memory is entirely held by another allocator (such as a
+ * framework's caching pool), or a latency-critical loop where cudaMalloc and
+ * cudaFree, which can block and synchronise the device, are not allowed.
+ *
+ * The caller passes the graph directly (device off int64[n+1] and adj
+ * int32[nnz], no handle), the sources on the host and the outputs (device
+ * dist[n], masks[d][n]) exactly as for cbfs_run; the results are identical.
+ * The traversal's scratch is one fixed array compiled into the library
+ * (about 7 MB; every GPU that loads the library keeps it until the process
+ * exits), so the sizes are limited: n <= 131072 and nnz <= 4194304, larger
+ * graphs return CBFS_E_NOMEM.  The first call on a device looks up the
+ * array's device address for that device; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's contents (each call clears what must start at zero): calls that
+ * overlap on the GPU -- on other streams or from other host threads -- race
+ * and corrupt each other's results.  The edge phase runs in push mode only.
+ * The call synchronises `stream`; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ */
+int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* adj, int64_t nnz, const int32_t* host_sources,
+                     int k, int d, uint8_t* dist, uint64_t* masks, void* stream);
+
+/*
  * Work counters (Theorem 1) of C clusters computed from their outputs
  * (device dist[C][n], masks[C][d][n], host_ks[C] cluster sizes) on the
  * resident graph g, written to host_out[C].  Each frontier appearance of

@@ -61,6 +61,7 @@ SIGNATURES = {
     "cbfs_graph_info": (_I, [_P, _P, _P]),
     "cbfs_run": (_I, [_P, _P, _I, _I, _P, _P, _P]),
     "cbfs_run_batched": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "cbfs_run_noalloc": (_I, [_I64, _P, _P, _I64, _P, _I, _I, _P, _P, _P]),
     "cbfs_output_stats": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
     "cbfs_profile": (_I, [_P, _I, _P]),
     "cbfs_labels_create": (_I, [_I64, _I, _I, _SZ, _P]),
@@ -243,6 +244,23 @@ class Graph:
         _check(rc, "cbfs_output_stats")
         return np.array([[o.frontier_appearances, o.arcs_scanned, o.reached_arcs, o.rounds] for o in out[:C]],
                         dtype=np.int64).reshape(C, 4)
+
+
+def run_noalloc(off: torch.Tensor, adj: torch.Tensor, sources, d: int, dist: torch.Tensor, masks: torch.Tensor,
+                stream=None):
+    """``cbfs_run_noalloc``: one C-BFS for callers that cannot allocate device
+    memory.  ``off`` (int64, n+1) and ``adj`` (int32) are CUDA tensors the
+    caller owns; ``dist`` (uint8, n) and ``masks`` (int64, d x n) are
+    preallocated CUDA tensors that receive the outputs.  The library uses a
+    fixed scratch array (n <= 131072, nnz <= 4194304) shared by all calls, so
+    calls must not overlap on the GPU."""
+    S = _host_i32(sources)
+    n = off.numel() - 1
+    rc = lib().cbfs_run_noalloc(int(n), _ptr(off), _ptr(adj) if adj.numel() else None, int(adj.numel()),
+                                S.ctypes.data, int(S.size), int(d), _ptr(dist), _ptr(masks) if d > 0 else None,
+                                _stream_ptr(stream))
+    _check(rc, "cbfs_run_noalloc")
+    return dist, masks
 
 
 class Labels:

@@ -116,7 +116,14 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long x, un
     return s;  // valid in thread 0
 }
 
+}  // namespace
+
 // --------------------------------------------------------------- kernels
+// The four traversal kernels have external linkage (declared in
+// cbfs_internal.cuh) so that every entry point of the library launches the
+// same code.
+
+namespace cbfs {
 
 // Seeds a wave: acc[S[j]] = bit j and F_0 = S for every slot.
 // seeds[i] = slot << 40 | j << 32 | vertex.
@@ -257,6 +264,10 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     }
 }
 
+}  // namespace cbfs
+
+namespace {
+
 __device__ __forceinline__ void push_arc(const SlotDesc& S, int s, uint64_t fw, int32_t v, uint64_t* qn,
                                          unsigned long long* qlen_next) {
     ulonglong2* p = S.va + v;
@@ -275,6 +286,10 @@ __device__ __forceinline__ bool decide_pull(const Wave& w, const RoundCtl* c) {
     const double work = (double)c->nf + (double)c->sdeg;
     return work > (double)w.alpha * (double)w.nnz * (double)w.nslots;
 }
+
+}  // namespace
+
+namespace cbfs {
 
 // Phase B: the edge phase of round `round`.
 __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
@@ -443,6 +458,10 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
         }
     }
 }
+
+}  // namespace cbfs
+
+namespace {
 
 // Graph validation: ids in range, no self loop, strictly increasing lists,
 // every arc has its reverse.  flag = 1 on the first failure.

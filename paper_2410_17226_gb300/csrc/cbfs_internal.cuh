@@ -84,6 +84,12 @@ struct Wave {
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
+// Traversal kernels (cbfs_core.cu).  seeds[i] = slot << 40 | j << 32 | vertex.
+__global__ void k_seed(Wave w, const uint64_t* seeds, int count);
+__global__ void k_check_sources(Wave w, const uint64_t* seeds, int count);
+__global__ void k_phase_a(Wave w, int round);
+__global__ void k_phase_b(Wave w, int round);
+
 }  // namespace cbfs
 
 // Implemented in cbfs_core.cu; used by cbfs_labels.cu.
