@@ -1,30 +1,35 @@
 // libcbfs.so, part 1: graph residency, the Cluster-BFS traversal and its
 // C ABI entry points (include/cbfs.h).
 //
-// The traversal follows Algorithm 1 (Section 3.2) level by level.  Round i
-// has two kernels:
+// The traversal follows Algorithm 1 (Section 3.2) level by level for P
+// clusters at once ("slots"; P = 1, 2, 4 or 8).  The per-vertex state is
+// vertex-major -- vis[v][0..P) and acc[v][0..P) -- so one scan of an
+// adjacency list and one gathered block of P subset words serve every
+// cluster in flight.  Round i has two kernels:
 //
-//   phase A (vertex phase): for every queue entry (cluster slot s, vertex u)
-//     new = acc[u] & ~visit[u]; visit[u] |= new; acc[u] = 0;
-//     Delta_u = i on the first visit;  S_u[i - Delta_u] = new  (stored when
-//     i - Delta_u < d; > d means the cluster diameter exceeds d).
-//     Entries with new sources are compacted per 1024-entry tile with their
-//     arc prefix; lists longer than kBigDeg go to a "big" list cut into
+//   phase A (vertex phase): for every queued vertex u and slot s
+//     new = acc[u][s] & ~vis[u][s]; vis[u][s] |= new; acc[u][s] = 0;
+//     Delta_u = i on the first visit of slot s;  S_u[i - Delta_u] = new
+//     (stored when i - Delta_u < d; > d means the cluster diameter exceeds
+//     d).  Vertices with new sources are compacted per tile with their arc
+//     prefix; lists longer than kBigDeg go to a "big" list cut into
 //     kBigDeg-arc pieces.
 //
 //   phase B (edge phase), one of
 //     push (EdgeMap-Sparse, Appendix A): every frontier arc (u, v) ORs the
-//       new sources of u into acc[v] when they are not already in visit[v]
-//       or acc[v] (checked before the atomic); the pusher that turns acc[v]
-//       from 0 to non-zero appends v to F_{i+1} -- the once-per-round claim
-//       that r[v] implements in Algorithm 1.  Arcs are spread evenly over
-//       the CTAs: big-list pieces first, then tiles whose entries are
-//       located by a binary search of the tile's arc prefix in shared memory.
-//     pull (EdgeMap-Dense): every vertex v whose visit is not ALL ORs the
-//       visit words of all its neighbours (sources at distance <= i from a
-//       neighbour are at distance <= i+1 from v), stops early once ALL is
-//       covered, and keeps the part not in visit[v] as acc[v].  Vertices are
-//       handled by a thread, a warp or a CTA according to their degree.
+//       new sources of u into acc[v] where they are not in vis[v] or
+//       acc[v] (both checked before the atomic); a pusher that turns some
+//       acc[v][s] from 0 to non-zero claims v for F_{i+1} -- the
+//       once-per-round claim that r[v] implements in Algorithm 1.  Arcs are
+//       spread evenly over the CTAs: big-list pieces first, then tiles whose
+//       entries are found by a binary search of the tile's arc prefix in
+//       shared memory.
+//     pull (EdgeMap-Dense): every vertex v with some unfinished slot ORs the
+//       vis blocks of all its neighbours (sources at distance <= i from a
+//       neighbour are at distance <= i+1 from v), stops early once every
+//       unfinished slot is covered, and keeps the part not in vis[v] as
+//       acc[v].  Vertices are handled by a thread, a warp or a CTA according
+//       to their degree, each lane keeping four gathers in flight.
 //     The direction is chosen per round from |F| + sum deg(F) against
 //     pull_alpha * nnz (the rule of Algorithm "EdgeMap").
 //
@@ -35,12 +40,9 @@
 //     at v by Sseen[u] must be at distance exactly i from u, so both pushes
 //     set the same bits;
 //   - the edge condition i - Delta_v < d of Algorithm 1 is replaced by the
-//     test new & ~visit[v] & ~acc[v] != 0, which is empty whenever the
-//     condition fails (by Corollary 1 visit[v] = ALL after round Delta_v + d)
+//     test new & ~vis[v] & ~acc[v] != 0, which is empty whenever the
+//     condition fails (by Corollary 1 vis[v] = ALL after round Delta_v + d)
 //     and also skips arcs that would not change Snext[v].
-//
-// Several clusters ("slots") are traversed in lockstep: queue entries carry
-// their slot and each slot has its own state and outputs.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -55,7 +57,8 @@ namespace {
 
 // ----------------------------------------------------------------- helpers
 
-__device__ __forceinline__ void append(uint64_t* q, unsigned long long* qlen, uint64_t entry) {
+template <class T>
+__device__ __forceinline__ void append(T* q, unsigned long long* qlen, T entry) {
     const unsigned mask = __activemask();
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(mask) - 1;
@@ -116,26 +119,151 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long x, un
     return s;  // valid in thread 0
 }
 
+// P consecutive words (P * 8 bytes, aligned to min(P * 8, 16)).
+template <int P>
+__device__ __forceinline__ void load_words(const uint64_t* p, uint64_t (&x)[P]) {
+    if constexpr (P == 1) {
+        x[0] = p[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; i += 2) {
+            const ulonglong2 t = reinterpret_cast<const ulonglong2*>(p)[i / 2];
+            x[i] = t.x;
+            x[i + 1] = t.y;
+        }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void store_words(uint64_t* p, const uint64_t (&x)[P]) {
+    if constexpr (P == 1) {
+        p[0] = x[0];
+    } else {
+#pragma unroll
+        for (int i = 0; i < P; i += 2) reinterpret_cast<ulonglong2*>(p)[i / 2] = make_ulonglong2(x[i], x[i + 1]);
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void zero_words(uint64_t* p) {
+    uint64_t z[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) z[i] = 0;
+    store_words<P>(p, z);
+}
+
+// ORs the vis blocks of up to four neighbours adj[e .. min(e + 4 * step, o1))
+// taken every `step` arcs into acc; all four gathers are issued before any
+// is used.
+template <int P>
+__device__ __forceinline__ void gather4(const Wave& w, int64_t e, int64_t step, int64_t o1, uint64_t (&acc)[P]) {
+    int32_t u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = (e + k * step < o1) ? w.adj[e + k * step] : -1;
+    uint64_t x[4][P];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (u[k] >= 0) load_words<P>(w.vis + (size_t)u[k] * P, x[k]);
+        else {
+#pragma unroll
+            for (int s = 0; s < P; ++s) x[k][s] = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int s = 0; s < P; ++s) acc[s] |= x[k][s];
+}
+
+// Push the new sources fw[0..P) of a frontier vertex along one arc to t.
+template <int P>
+__device__ __forceinline__ void push_arc(const Wave& w, const uint64_t* fw, uint32_t t, uint32_t stamp, uint32_t* qn,
+                                         unsigned long long* qlen_next) {
+    uint64_t vs[P], b[P];
+    load_words<P>(w.vis + (size_t)t * P, vs);  // vis is read-only in phase B
+    uint64_t any = 0;
+#pragma unroll
+    for (int s = 0; s < P; ++s) {
+        b[s] = fw[s] & ~vs[s];
+        any |= b[s];
+    }
+    if (!any) return;
+    uint64_t* ap = w.acc + (size_t)t * P;
+    uint64_t ac[P];
+    load_words<P>(ap, ac);  // acc only grows in phase B: a stale copy is a subset
+    bool claim = false;
+#pragma unroll
+    for (int s = 0; s < P; ++s) {
+        const uint64_t bb = b[s] & ~ac[s];
+        if (bb) {
+            const unsigned long long old = atomicOr(reinterpret_cast<unsigned long long*>(ap + s), (unsigned long long)bb);
+            claim |= (old == 0ull);
+        }
+    }
+    if (!claim) return;
+    if (P == 1 || atomicExch(w.rq + t, stamp) != stamp) append(qn, qlen_next, t);
+}
+
+__device__ __forceinline__ bool decide_pull(const Wave& w, const RoundCtl* c) {
+    if (!(w.alpha > 0.f)) return false;
+    const double work = (double)c->nf + (double)c->sdeg;
+    return work > (double)w.alpha * (double)w.nnz;
+}
+
+// Bits still missing at v over the unfinished slots um.
+template <int P>
+__device__ __forceinline__ uint64_t missing_bits(const uint64_t (&acc)[P], const uint64_t (&vs)[P], const uint64_t (&all)[P],
+                                                 unsigned int um) {
+    uint64_t rem = 0;
+#pragma unroll
+    for (int s = 0; s < P; ++s)
+        if ((um >> s) & 1u) rem |= all[s] & ~(acc[s] | vs[s]);
+    return rem;
+}
+
+template <int P>
+__device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], const uint64_t (&all)[P], unsigned int active) {
+    unsigned int um = 0;
+#pragma unroll
+    for (int s = 0; s < P; ++s)
+        if (((active >> s) & 1u) && vs[s] != all[s]) um |= 1u << s;
+    return um;
+}
+
+// Pull result of v: keep the new part as acc[v] and queue v.
+template <int P>
+__device__ __forceinline__ void pull_finish(const Wave& w, int32_t v, const uint64_t (&acc)[P], const uint64_t (&vs)[P],
+                                            uint32_t* qn, unsigned long long* qlen_next) {
+    uint64_t nw[P], any = 0;
+#pragma unroll
+    for (int s = 0; s < P; ++s) {
+        nw[s] = acc[s] & ~vs[s];
+        any |= nw[s];
+    }
+    if (any) {
+        store_words<P>(w.acc + (size_t)v * P, nw);
+        append(qn, qlen_next, (uint32_t)v);
+    }
+}
+
 }  // namespace
 
 // --------------------------------------------------------------- kernels
-// The four traversal kernels have external linkage (declared in
+// The traversal kernels have external linkage (declared in
 // cbfs_internal.cuh) so that every entry point of the library launches the
 // same code.
 
 namespace cbfs {
 
-// Seeds a wave: acc[S[j]] = bit j and F_0 = S for every slot.
-// seeds[i] = slot << 40 | j << 32 | vertex.
+// Seeds a wave: acc[v][s] = bit j for S_s[j] = v, F_0 = the distinct sources.
 __global__ void k_seed(Wave w, const uint64_t* seeds, int count) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const uint64_t e = seeds[i];
         const int s = (int)((e >> 40) & 0xFF), j = (int)((e >> 32) & 0xFF);
         const uint32_t v = (uint32_t)e;
-        w.slots[s].va[v].y = 1ull << j;
-        w.q0[i] = ((uint64_t)s << 32) | v;
+        w.acc[(size_t)v * w.P + s] = 1ull << j;  // (v, s) is unique within a wave
+        if (atomicExch(w.rq + v, 1u) != 1u) append(w.q0, &w.ctl[0].qlen, v);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) w.ctl[0].qlen = (unsigned long long)count;
 }
 
 // After a wave: every source must have seen every source of its cluster.
@@ -146,76 +274,85 @@ __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count) {
         const uint64_t e = seeds[i];
         const int s = (int)((e >> 40) & 0xFF);
         const uint32_t v = (uint32_t)e;
-        const SlotDesc sd = w.slots[s];
-        if (sd.va[v].x != sd.all) set_status(w.status, CBFS_E_DIAMETER);
+        if (w.vis[(size_t)v * w.P + s] != w.slots[s].all) set_status(w.status, CBFS_E_DIAMETER);
     }
 }
 
 // Phase A: the vertex phase of round `round` and the push work lists.
+template <int P>
 __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
-    __shared__ SlotDesc ss[kMaxSlots];
+    constexpr int EPT = Geo<P>::kEpt;
+    constexpr int TILE = Geo<P>::kTile;
+    __shared__ SlotDesc ss[P];
     __shared__ ScanSmem scan;
     __shared__ unsigned long long red[kWarps];
     __shared__ unsigned int s_active;
     RoundCtl* c = w.ctl + round;
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
-    for (int i = threadIdx.x; i < w.nslots; i += kThreads) ss[i] = w.slots[i];
+    if (threadIdx.x < w.nslots) ss[threadIdx.x] = w.slots[threadIdx.x];
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
-    const uint64_t* q = (round & 1) ? w.q1 : w.q0;
-    const unsigned long long ntiles = (qlen + kTile - 1) / kTile;
+    const uint32_t* q = (round & 1) ? w.q1 : w.q0;
+    const unsigned long long ntiles = (qlen + TILE - 1) / TILE;
     unsigned long long my_nf = 0, my_sdeg = 0;
     unsigned int my_active = 0;
     for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        uint32_t keep[kPerThread], dg[kPerThread], sl[kPerThread];
-        int64_t ost[kPerThread];
-        uint64_t fw[kPerThread];
+        uint32_t keep[EPT], dg[EPT];
+        int64_t ost[EPT];
+        uint64_t fw[EPT][P];
         uint32_t cnt = 0, arcs = 0;
 #pragma unroll
-        for (int r = 0; r < kPerThread; ++r) {
+        for (int r = 0; r < EPT; ++r) {
             keep[r] = 0;
             dg[r] = 0;
-            sl[r] = 0;
             ost[r] = 0;
-            fw[r] = 0;
-            const unsigned long long idx = t * kTile + (unsigned long long)threadIdx.x * kPerThread + r;
+#pragma unroll
+            for (int s = 0; s < P; ++s) fw[r][s] = 0;
+            const unsigned long long idx = t * TILE + (unsigned long long)threadIdx.x * EPT + r;
             if (idx >= qlen) continue;
-            const uint64_t e = q[idx];
-            const int s = (int)(e >> 32);
-            const uint32_t u = (uint32_t)e;
-            const SlotDesc& S = ss[s];
-            const ulonglong2 st = S.va[u];
-            const uint64_t nw = st.y & ~st.x;
-            if (st.y) S.va[u] = make_ulonglong2(st.x | nw, 0ull);
-            if (!nw) continue;
+            const uint32_t u = q[idx];
+            uint64_t a[P], vs[P];
+            load_words<P>(w.acc + (size_t)u * P, a);
+            load_words<P>(w.vis + (size_t)u * P, vs);
+            uint64_t any = 0;
+#pragma unroll
+            for (int s = 0; s < P; ++s) {
+                fw[r][s] = a[s] & ~vs[s];
+                any |= fw[r][s];
+                vs[s] |= fw[r][s];
+            }
+            store_words<P>(w.vis + (size_t)u * P, vs);
+            zero_words<P>(w.acc + (size_t)u * P);
+            if (!any) continue;
+#pragma unroll
+            for (int s = 0; s < P; ++s) {
+                if (!fw[r][s]) continue;
+                const SlotDesc& S = ss[s];
+                const uint8_t dd = S.dist[u];
+                int j;
+                if (dd == 0xFF) {
+                    if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
+                    else S.dist[u] = (uint8_t)round;
+                    j = 0;
+                } else {
+                    j = round - (int)dd;
+                }
+                if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = fw[r][s];
+                else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
+                my_active |= 1u << s;
+            }
             const int64_t o0 = w.off[u], o1 = w.off[u + 1];
             const int64_t deg = o1 - o0;
-            const uint8_t dd = S.dist[u];
-            int j;
-            if (dd == 0xFF) {
-                if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
-                else S.dist[u] = (uint8_t)round;
-                j = 0;
-            } else {
-                j = round - (int)dd;
-            }
-            if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = nw;
-            else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
             my_nf += 1;
             my_sdeg += (unsigned long long)deg;
-            my_active |= 1u << s;
             if (deg == 0) continue;
             if (deg > kBigDeg) {
                 // big list: one entry plus ceil(deg / kBigDeg) piece records
                 const unsigned int bi = atomicAdd(&c->nbig, 1u);
-                BigEntry be;
-                be.ost = o0;
-                be.deg = deg;
-                be.fw = nw;
-                be.slot = s;
-                be.pad = 0;
-                w.big[bi] = be;
+                w.big[bi].ost = o0;
+                w.big[bi].deg = deg;
+                store_words<P>(w.big_fw + (size_t)bi * P, fw[r]);
                 const unsigned int np = (unsigned int)((deg + kBigDeg - 1) / kBigDeg);
                 const unsigned int p0 = atomicAdd(&c->npieces, np);
                 for (unsigned int p = 0; p < np; ++p) {
@@ -226,23 +363,20 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             }
             keep[r] = 1;
             dg[r] = (uint32_t)deg;
-            sl[r] = (uint32_t)s;
             ost[r] = o0;
-            fw[r] = nw;
             cnt += 1;
             arcs += (uint32_t)deg;
         }
         uint32_t ecnt, earcs, tcnt, tarcs;
         block_scan2(cnt, arcs, ecnt, earcs, tcnt, tarcs, scan);
-        const unsigned long long base = t * kTile;
+        const unsigned long long base = t * TILE;
 #pragma unroll
-        for (int r = 0; r < kPerThread; ++r) {
+        for (int r = 0; r < EPT; ++r) {
             if (!keep[r]) continue;
             const unsigned long long pos = base + ecnt;
             w.t_pre[pos] = earcs;
             w.t_ost[pos] = ost[r];
-            w.t_fw[pos] = fw[r];
-            w.t_slot[pos] = (uint8_t)sl[r];
+            store_words<P>(w.t_fw + pos * P, fw[r]);
             ecnt += 1;
             earcs += dg[r];
         }
@@ -264,50 +398,24 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     }
 }
 
-}  // namespace cbfs
-
-namespace {
-
-__device__ __forceinline__ void push_arc(const SlotDesc& S, int s, uint64_t fw, int32_t v, uint64_t* qn,
-                                         unsigned long long* qlen_next) {
-    ulonglong2* p = S.va + v;
-    const ulonglong2 st = *p;  // visit is read-only in phase B; acc only grows, a stale copy is a subset
-    const uint64_t b = fw & ~st.x & ~st.y;
-    bool app = false;
-    if (b) {
-        const unsigned long long old = atomicOr(reinterpret_cast<unsigned long long*>(&p->y), (unsigned long long)b);
-        app = (old == 0ull);
-    }
-    if (app) append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
-}
-
-__device__ __forceinline__ bool decide_pull(const Wave& w, const RoundCtl* c) {
-    if (!(w.alpha > 0.f)) return false;
-    const double work = (double)c->nf + (double)c->sdeg;
-    return work > (double)w.alpha * (double)w.nnz * (double)w.nslots;
-}
-
-}  // namespace
-
-namespace cbfs {
-
 // Phase B: the edge phase of round `round`.
+template <int P>
 __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
-    __shared__ SlotDesc ss[kMaxSlots];
+    constexpr int TILE = Geo<P>::kTile;
     __shared__ uint32_t spre[kThreads + 1];
     __shared__ int64_t sost[kThreads];
-    __shared__ uint64_t sfw[kThreads];
-    __shared__ uint8_t sslot[kThreads];
+    __shared__ uint64_t sfw[kThreads * P];
+    __shared__ uint64_t sall[P];
     __shared__ unsigned int s_work;
-    __shared__ uint64_t sor[kWarps];
-    __shared__ int s_done;
+    __shared__ uint64_t sor[kWarps][P];
     RoundCtl* c = w.ctl + round;
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
-    for (int i = threadIdx.x; i < w.nslots; i += kThreads) ss[i] = w.slots[i];
+    if (threadIdx.x < P) sall[threadIdx.x] = (int)threadIdx.x < w.nslots ? w.slots[threadIdx.x].all : 0ull;
     __syncthreads();
-    uint64_t* qn = (round & 1) ? w.q0 : w.q1;
+    uint32_t* qn = (round & 1) ? w.q0 : w.q1;
     unsigned long long* qlen_next = &w.ctl[round + 1].qlen;
+    const uint32_t stamp = (uint32_t)round + 2;  // F_{round+1}
     const bool pull = decide_pull(w, c);
     if (blockIdx.x == 0 && threadIdx.x == 0) c->mode = pull ? 1 : 0;
 
@@ -318,17 +426,18 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
             if (threadIdx.x == 0) s_work = atomicAdd(&c->piece_ctr, 1u);
             __syncthreads();
             const unsigned int p = s_work;
+            if (p < npieces && threadIdx.x < P) sfw[threadIdx.x] = w.big_fw[(size_t)w.piece_ent[p] * P + threadIdx.x];
             __syncthreads();
             if (p >= npieces) break;
             const BigEntry be = w.big[w.piece_ent[p]];
             const int64_t a0 = (int64_t)w.piece_no[p] * kBigDeg;
             const int64_t a1 = min(be.deg, a0 + kBigDeg);
-            const SlotDesc& S = ss[be.slot];
             for (int64_t a = a0 + threadIdx.x; a < a1; a += kThreads)
-                push_arc(S, be.slot, be.fw, w.adj[be.ost + a], qn, qlen_next);
+                push_arc<P>(w, sfw, (uint32_t)w.adj[be.ost + a], stamp, qn, qlen_next);
+            __syncthreads();
         }
         // tiles: entries of degree <= kBigDeg, arcs spread over the threads
-        const unsigned long long ntiles = (qlen + kTile - 1) / kTile;
+        const unsigned long long ntiles = (qlen + TILE - 1) / TILE;
         for (;;) {
             if (threadIdx.x == 0) s_work = atomicAdd(&c->tile_ctr, 1u);
             __syncthreads();
@@ -337,16 +446,15 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
             if (t >= ntiles) break;
             const uint32_t cnt = w.tile_cnt[t];
             const uint32_t tarcs = w.tile_arcs[t];
-            const unsigned long long base = t * kTile;
+            const unsigned long long base = t * TILE;
             for (uint32_t g0 = 0; g0 < cnt; g0 += kThreads) {
                 const uint32_t ge = min((uint32_t)kThreads, cnt - g0);
                 if (threadIdx.x < ge) {
                     const unsigned long long pos = base + g0 + threadIdx.x;
                     spre[threadIdx.x] = w.t_pre[pos];
                     sost[threadIdx.x] = w.t_ost[pos];
-                    sfw[threadIdx.x] = w.t_fw[pos];
-                    sslot[threadIdx.x] = w.t_slot[pos];
                 }
+                for (uint32_t i = threadIdx.x; i < ge * P; i += kThreads) sfw[i] = w.t_fw[(base + g0) * P + i];
                 if (threadIdx.x == 0) spre[ge] = (g0 + ge < cnt) ? w.t_pre[base + g0 + ge] : tarcs;
                 __syncthreads();
                 const uint32_t a_lo = spre[0], a_hi = spre[ge];
@@ -358,8 +466,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
                         if (spre[mid] <= a) lo = mid;
                         else hi = mid - 1;
                     }
-                    const int s = sslot[lo];
-                    push_arc(ss[s], s, sfw[lo], w.adj[sost[lo] + (a - spre[lo])], qn, qlen_next);
+                    push_arc<P>(w, sfw + lo * P, (uint32_t)w.adj[sost[lo] + (a - spre[lo])], stamp, qn, qlen_next);
                 }
                 __syncthreads();
             }
@@ -369,42 +476,40 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
 
     // ---- pull: dense pass over every vertex that can still gain sources
     const unsigned int active = c->slot_active;
+    uint64_t all[P];
+#pragma unroll
+    for (int s = 0; s < P; ++s) all[s] = sall[s];
     // CTA per high-degree vertex
     for (int64_t i = blockIdx.x; i < w.n_big; i += gridDim.x) {
         const int32_t v = w.pl_big[i];
+        uint64_t vs[P];
+        load_words<P>(w.vis + (size_t)v * P, vs);
+        const unsigned int um = unfinished<P>(vs, all, active);
+        if (!um) continue;  // uniform across the block
         const int64_t o0 = w.off[v], o1 = w.off[v + 1];
-        for (int s = 0; s < w.nslots; ++s) {
-            if (!((active >> s) & 1u)) continue;
-            const SlotDesc& S = ss[s];
-            const uint64_t vis = S.va[v].x;
-            if (vis == S.all) continue;
-            uint64_t acc = 0;
-            for (int64_t b0 = o0; b0 < o1; b0 += kThreads) {
-                const int64_t e = b0 + threadIdx.x;
-                if (e < o1) acc |= S.va[w.adj[e]].x;
-                const uint64_t wacc = warp_or(acc);
-                if ((threadIdx.x & 31) == 0) sor[threadIdx.x >> 5] = wacc;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    uint64_t x = 0;
-                    for (int k = 0; k < kWarps; ++k) x |= sor[k];
-                    s_done = ((x | vis) == S.all);
-                    sor[0] = x;
-                }
-                __syncthreads();
-                acc = sor[0];
-                const int done = s_done;
-                __syncthreads();
-                if (done) break;
+        uint64_t acc[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) acc[s] = 0;
+        for (int64_t b0 = o0; b0 < o1; b0 += 4 * kThreads) {
+            gather4<P>(w, b0 + threadIdx.x, kThreads, o1, acc);
+#pragma unroll
+            for (int s = 0; s < P; ++s) {
+                const uint64_t wa = warp_or(acc[s]);
+                if ((threadIdx.x & 31) == 0) sor[threadIdx.x >> 5][s] = wa;
             }
-            if (threadIdx.x == 0) {
-                const uint64_t nw = acc & ~vis;
-                if (nw) {
-                    S.va[v].y = nw;
-                    append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
-                }
+            __syncthreads();
+            if (threadIdx.x < P) {
+                uint64_t x = 0;
+                for (int k = 0; k < kWarps; ++k) x |= sor[k][threadIdx.x];
+                sor[0][threadIdx.x] = x;
             }
+            __syncthreads();
+#pragma unroll
+            for (int s = 0; s < P; ++s) acc[s] = sor[0][s];
+            __syncthreads();
+            if (missing_bits<P>(acc, vs, all, um) == 0) break;
         }
+        if (threadIdx.x == 0) pull_finish<P>(w, v, acc, vs, qn, qlen_next);
     }
     // warp per mid-degree vertex
     {
@@ -413,50 +518,67 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
         const int64_t nw_total = ((int64_t)gridDim.x * kThreads) >> 5;
         for (int64_t i = gw; i < w.n_mid; i += nw_total) {
             const int32_t v = w.pl_mid[i];
+            uint64_t vs[P];
+            load_words<P>(w.vis + (size_t)v * P, vs);
+            const unsigned int um = unfinished<P>(vs, all, active);
+            if (!um) continue;
             const int64_t o0 = w.off[v], o1 = w.off[v + 1];
-            for (int s = 0; s < w.nslots; ++s) {
-                if (!((active >> s) & 1u)) continue;
-                const SlotDesc& S = ss[s];
-                const uint64_t vis = S.va[v].x;
-                if (vis == S.all) continue;
-                uint64_t acc = 0;
-                for (int64_t b0 = o0; b0 < o1; b0 += 32) {
-                    const int64_t e = b0 + lane;
-                    if (e < o1) acc |= S.va[w.adj[e]].x;
-                    acc = warp_or(acc);
-                    if ((acc | vis) == S.all) break;
-                }
-                if (lane == 0) {
-                    const uint64_t nw = acc & ~vis;
-                    if (nw) {
-                        S.va[v].y = nw;
-                        append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
-                    }
-                }
+            uint64_t acc[P];
+#pragma unroll
+            for (int s = 0; s < P; ++s) acc[s] = 0;
+            for (int64_t b0 = o0; b0 < o1; b0 += 128) {
+                gather4<P>(w, b0 + lane, 32, o1, acc);
+#pragma unroll
+                for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
+                if (missing_bits<P>(acc, vs, all, um) == 0) break;
             }
+            if (lane == 0) pull_finish<P>(w, v, acc, vs, qn, qlen_next);
         }
     }
     // thread per low-degree vertex
     for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < w.n_small; i += (int64_t)gridDim.x * kThreads) {
         const int32_t v = w.pl_small[i];
+        uint64_t vs[P];
+        load_words<P>(w.vis + (size_t)v * P, vs);
+        const unsigned int um = unfinished<P>(vs, all, active);
+        if (!um) continue;
         const int64_t o0 = w.off[v], o1 = w.off[v + 1];
-        for (int s = 0; s < w.nslots; ++s) {
-            if (!((active >> s) & 1u)) continue;
-            const SlotDesc& S = ss[s];
-            const uint64_t vis = S.va[v].x;
-            if (vis == S.all) continue;
-            uint64_t acc = 0;
-            for (int64_t e = o0; e < o1; ++e) {
-                acc |= S.va[w.adj[e]].x;
-                if ((acc | vis) == S.all) break;
-            }
-            const uint64_t nw = acc & ~vis;
-            if (nw) {
-                S.va[v].y = nw;
-                append(qn, qlen_next, ((uint64_t)s << 32) | (uint32_t)v);
-            }
+        uint64_t acc[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) acc[s] = 0;
+        for (int64_t e = o0; e < o1; e += 4) {
+            gather4<P>(w, e, 1, o1, acc);
+            if (missing_bits<P>(acc, vs, all, um) == 0) break;
         }
+        pull_finish<P>(w, v, acc, vs, qn, qlen_next);
     }
+}
+
+template __global__ void k_phase_a<1>(Wave, int);
+template __global__ void k_phase_a<2>(Wave, int);
+template __global__ void k_phase_a<4>(Wave, int);
+template __global__ void k_phase_a<8>(Wave, int);
+template __global__ void k_phase_b<1>(Wave, int);
+template __global__ void k_phase_b<2>(Wave, int);
+template __global__ void k_phase_b<4>(Wave, int);
+template __global__ void k_phase_b<8>(Wave, int);
+
+cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which) {
+    switch (w.P) {
+#define CBFS_CASE(PP)                                                       \
+    case PP:                                                                \
+        if (which == 0) k_phase_a<PP><<<grid, kThreads, 0, st>>>(w, round); \
+        else k_phase_b<PP><<<grid, kThreads, 0, st>>>(w, round);            \
+        break;
+        CBFS_CASE(1)
+        CBFS_CASE(2)
+        CBFS_CASE(4)
+        CBFS_CASE(8)
+#undef CBFS_CASE
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace cbfs
@@ -464,24 +586,44 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
 namespace {
 
 // Graph validation: ids in range, no self loop, strictly increasing lists,
-// every arc has its reverse.  flag = 1 on the first failure.
-__global__ void k_validate(int64_t n, const int64_t* off, const int32_t* adj, int* flag) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o0 = off[v], o1 = off[v + 1];
-        int32_t prev = -1;
-        for (int64_t e = o0; e < o1; ++e) {
-            const int32_t u = adj[e];
-            if (u < 0 || (int64_t)u >= n || (int64_t)u == v || u <= prev) { atomicExch(flag, 1); return; }
-            prev = u;
-            int64_t lo = off[u], hi = off[u + 1];
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                if ((int64_t)adj[mid] < v) lo = mid + 1;
-                else hi = mid;
-            }
-            if (lo >= off[u + 1] || (int64_t)adj[lo] != v) { atomicExch(flag, 1); return; }
-        }
+// every arc has its reverse (binary search in the neighbour's list).  One
+// thread, warp or CTA per vertex by degree class; flag = 1 on any failure.
+__device__ __forceinline__ bool arc_ok(int64_t n, const int64_t* off, const int32_t* adj, int64_t v, int64_t e,
+                                       int64_t o0) {
+    const int32_t u = adj[e];
+    if (u < 0 || (int64_t)u >= n || (int64_t)u == v) return false;
+    if (e > o0 && adj[e - 1] >= u) return false;
+    int64_t lo = off[u], hi = off[u + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)adj[mid] < v) lo = mid + 1;
+        else hi = mid;
     }
+    return lo < off[u + 1] && (int64_t)adj[lo] == v;
+}
+
+__global__ void k_validate(int64_t n, const int64_t* off, const int32_t* adj, const int32_t* pl_small, int64_t n_small,
+                           const int32_t* pl_mid, int64_t n_mid, const int32_t* pl_big, int64_t n_big, int* flag) {
+    bool ok = true;
+    for (int64_t i = blockIdx.x; i < n_big; i += gridDim.x) {
+        const int64_t v = pl_big[i];
+        const int64_t o0 = off[v], o1 = off[v + 1];
+        for (int64_t e = o0 + threadIdx.x; e < o1; e += blockDim.x) ok &= arc_ok(n, off, adj, v, e, o0);
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < n_mid; i += nwarps) {
+        const int64_t v = pl_mid[i];
+        const int64_t o0 = off[v], o1 = off[v + 1];
+        for (int64_t e = o0 + lane; e < o1; e += 32) ok &= arc_ok(n, off, adj, v, e, o0);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_small; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = pl_small[i];
+        const int64_t o0 = off[v], o1 = off[v + 1];
+        for (int64_t e = o0; e < o1; ++e) ok &= arc_ok(n, off, adj, v, e, o0);
+    }
+    if (!ok) atomicExch(flag, 1);
 }
 
 // Work counters from outputs: per (cluster, vertex) the number of non-empty
@@ -540,20 +682,22 @@ struct cbfs_graph_s {
     int32_t* pl = nullptr;  // pull lists: small | mid | big
     int64_t n_small = 0, n_mid = 0, n_big = 0;
     int64_t big_vertices = 0, big_pieces = 0;
-    int grid = 0;
+    int grid_p[4] = {0, 0, 0, 0};  // phase-kernel grid for P = 1, 2, 4, 8 (SMs x resident CTAs)
     int device = 0;
     // scratch, sized for cap_slots clusters in flight
     int cap_slots = 0;
-    ulonglong2* va = nullptr;
-    uint64_t* q0 = nullptr;
-    uint64_t* q1 = nullptr;
+    uint64_t* vis = nullptr;
+    uint64_t* acc = nullptr;
+    uint32_t* rq = nullptr;
+    uint32_t* q0 = nullptr;
+    uint32_t* q1 = nullptr;
     uint32_t* t_pre = nullptr;
     int64_t* t_ost = nullptr;
     uint64_t* t_fw = nullptr;
-    uint8_t* t_slot = nullptr;
     uint32_t* tile_cnt = nullptr;
     uint32_t* tile_arcs = nullptr;
     BigEntry* big = nullptr;
+    uint64_t* big_fw = nullptr;
     uint32_t* piece_ent = nullptr;
     uint32_t* piece_no = nullptr;
     RoundCtl* ctl = nullptr;
@@ -615,16 +759,18 @@ void dev_free(T*& p) {
 }
 
 void free_scratch(cbfs_graph_s* g) {
-    dev_free(g->va);
+    dev_free(g->vis);
+    dev_free(g->acc);
+    dev_free(g->rq);
     dev_free(g->q0);
     dev_free(g->q1);
     dev_free(g->t_pre);
     dev_free(g->t_ost);
     dev_free(g->t_fw);
-    dev_free(g->t_slot);
     dev_free(g->tile_cnt);
     dev_free(g->tile_arcs);
     dev_free(g->big);
+    dev_free(g->big_fw);
     dev_free(g->piece_ent);
     dev_free(g->piece_no);
     g->cap_slots = 0;
@@ -633,22 +779,22 @@ void free_scratch(cbfs_graph_s* g) {
 int ensure_scratch(cbfs_graph_s* g, int P) {
     if (g->cap_slots >= P) return CBFS_OK;
     free_scratch(g);
-    const int64_t n = g->n;
-    const int64_t entries = (int64_t)P * n;
-    const int64_t tiles = (entries + kTile - 1) / kTile;
+    const ScratchSizes z = scratch_sizes(g->n, P);
     int rc = CBFS_OK;
-    if (!rc) rc = dev_alloc(&g->va, entries);
-    if (!rc) rc = dev_alloc(&g->q0, entries);
-    if (!rc) rc = dev_alloc(&g->q1, entries);
-    if (!rc) rc = dev_alloc(&g->t_pre, tiles * kTile);
-    if (!rc) rc = dev_alloc(&g->t_ost, tiles * kTile);
-    if (!rc) rc = dev_alloc(&g->t_fw, tiles * kTile);
-    if (!rc) rc = dev_alloc(&g->t_slot, tiles * kTile);
-    if (!rc) rc = dev_alloc(&g->tile_cnt, tiles);
-    if (!rc) rc = dev_alloc(&g->tile_arcs, tiles);
-    if (!rc) rc = dev_alloc(&g->big, (int64_t)P * g->big_vertices);
-    if (!rc) rc = dev_alloc(&g->piece_ent, (int64_t)P * g->big_pieces);
-    if (!rc) rc = dev_alloc(&g->piece_no, (int64_t)P * g->big_pieces);
+    if (!rc) rc = dev_alloc(&g->vis, z.state);
+    if (!rc) rc = dev_alloc(&g->acc, z.state);
+    if (!rc) rc = dev_alloc(&g->rq, z.queue);
+    if (!rc) rc = dev_alloc(&g->q0, z.queue);
+    if (!rc) rc = dev_alloc(&g->q1, z.queue);
+    if (!rc) rc = dev_alloc(&g->t_pre, z.list);
+    if (!rc) rc = dev_alloc(&g->t_ost, z.list);
+    if (!rc) rc = dev_alloc(&g->t_fw, z.list * P);
+    if (!rc) rc = dev_alloc(&g->tile_cnt, z.tiles);
+    if (!rc) rc = dev_alloc(&g->tile_arcs, z.tiles);
+    if (!rc) rc = dev_alloc(&g->big, g->big_vertices);
+    if (!rc) rc = dev_alloc(&g->big_fw, g->big_vertices * P);
+    if (!rc) rc = dev_alloc(&g->piece_ent, g->big_pieces);
+    if (!rc) rc = dev_alloc(&g->piece_no, g->big_pieces);
     if (rc) {
         free_scratch(g);
         return rc;
@@ -737,18 +883,29 @@ int check_clusters(const cbfs_graph_s* g, const int32_t* src, const int32_t* cof
     return CBFS_OK;
 }
 
+// Clusters per wave: the requested slot count rounded down to a power of
+// two (1, 2, 4, 8), no wider than the number of clusters.
+int slots_for(const cbfs_tune_t* tune, int C) {
+    int P = (tune && tune->slots > 0) ? tune->slots : 4;
+    P = std::min(P, kMaxSlots);
+    int p2 = 1;
+    while (p2 * 2 <= P) p2 *= 2;
+    while (p2 > 1 && p2 / 2 >= C) p2 /= 2;
+    return p2;
+}
+
 int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C, int d, uint8_t* dist,
                  uint64_t* masks, const cbfs_tune_t* tune, cudaStream_t st) {
     int rc = check_clusters(g, src, coff, C, d);
     if (rc) return rc;
     if (C == 0) return CBFS_OK;
     CK(cudaSetDevice(g->device));
-    int P = (tune && tune->slots > 0) ? tune->slots : 2;
-    P = std::max(1, std::min(P, std::min(C, kMaxSlots)));
-    float alpha = 0.1f;
+    const int P = slots_for(tune, C);
+    float alpha = 0.02f;
     if (tune && tune->pull_alpha != 0.f) alpha = tune->pull_alpha;
     rc = ensure_scratch(g, P);
     if (rc) return rc;
+    const int grid = g->grid_p[P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3];
     const int nwaves = (C + P - 1) / P;
     const int64_t total_src = coff[C];
     rc = ensure_dev(&g->slots, &g->slots_cap, (int64_t)nwaves * P);
@@ -768,7 +925,6 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
             memset(&sd, 0, sizeof(sd));
             if (c < C) {
                 const int k = coff[c + 1] - coff[c];
-                sd.va = g->va + (size_t)s * (size_t)n;
                 sd.dist = dist + (size_t)c * (size_t)n;
                 sd.masks = d ? masks + (size_t)c * (size_t)d * (size_t)n : nullptr;
                 sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
@@ -792,16 +948,20 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     w.off = g->off;
     w.adj = g->adj;
     w.d = d;
+    w.P = P;
+    w.vis = g->vis;
+    w.acc = g->acc;
+    w.rq = g->rq;
     w.q0 = g->q0;
     w.q1 = g->q1;
     w.ctl = g->ctl;
     w.t_pre = g->t_pre;
     w.t_ost = g->t_ost;
     w.t_fw = g->t_fw;
-    w.t_slot = g->t_slot;
     w.tile_cnt = g->tile_cnt;
     w.tile_arcs = g->tile_arcs;
     w.big = g->big;
+    w.big_fw = g->big_fw;
     w.piece_ent = g->piece_ent;
     w.piece_no = g->piece_no;
     w.pl_small = g->pl;
@@ -818,7 +978,9 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
         const int nsl = std::min(P, C - c0);
         w.nslots = nsl;
         w.slots = g->slots + (size_t)wv * P;
-        CK(cudaMemsetAsync(g->va, 0, sizeof(ulonglong2) * (size_t)nsl * (size_t)n, st));
+        CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
+        CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
+        CK(cudaMemsetAsync(g->rq, 0, sizeof(uint32_t) * (size_t)n, st));
         CK(cudaMemsetAsync(dist + (size_t)c0 * (size_t)n, 0xFF, (size_t)nsl * (size_t)n, st));
         if (d) CK(cudaMemsetAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, 0, sizeof(uint64_t) * (size_t)nsl * d * n, st));
         CK(cudaMemsetAsync(g->ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
@@ -830,12 +992,11 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
         bool done = false;
         for (int r = 0; r < kMaxRounds - 1 && !done; ++r) {
             ev = prof_begin(g, 1, st);
-            k_phase_a<<<g->grid, kThreads, 0, st>>>(w, r);
+            CK(launch_round(w, r, grid, st, 0));
             prof_end(g, ev, st);
             ev = prof_begin(g, 2, st);
-            k_phase_b<<<g->grid, kThreads, 0, st>>>(w, r);
+            CK(launch_round(w, r, grid, st, 1));
             prof_end(g, ev, st);
-            CK(cudaGetLastError());
             CK(cudaMemcpyAsync(&g->h_q[r + 1], &g->ctl[r + 1].qlen, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
             if (r % 2 == 1 || r == kMaxRounds - 2) {
                 CK(cudaStreamSynchronize(st));
@@ -924,7 +1085,7 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     if (nnz > 0 && cudaMemcpyAsync(g->adj, adj, sizeof(int32_t) * (size_t)nnz,
                                    inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess)
         return fail(CBFS_E_CUDA);
-    // degree classes for pull, capacity of the push big list
+    // degree classes for pull and validation, capacity of the push big list
     std::vector<int32_t> ls, lm, lb;
     for (int64_t v = 0; v < n; ++v) {
         const int64_t dg = h_off[v + 1] - h_off[v];
@@ -948,11 +1109,17 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
         cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, lb.data(), sizeof(int32_t) * lb.size(), cudaMemcpyHostToDevice, st);
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_phase_b, kThreads, 0);
-    g->grid = std::max(1, sms) * std::max(1, std::min(occ, 8));
+    const void* kb[4] = {(const void*)k_phase_b<1>, (const void*)k_phase_b<2>, (const void*)k_phase_b<4>,
+                         (const void*)k_phase_b<8>};
+    for (int i = 0; i < 4; ++i) {
+        occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb[i], kThreads, 0);
+        g->grid_p[i] = std::max(1, sms) * std::max(1, std::min(occ, 8));
+    }
     if (validate && n > 0) {
         if (cudaMemsetAsync(g->status, 0, sizeof(int), st) != cudaSuccess) return fail(CBFS_E_CUDA);
-        k_validate<<<std::max(1, sms) * 4, kThreads, 0, st>>>(n, g->off, g->adj, g->status);
+        k_validate<<<std::max(1, sms) * 8, kThreads, 0, st>>>(n, g->off, g->adj, g->pl, g->n_small, g->pl + g->n_small,
+                                                             g->n_mid, g->pl + g->n_small + g->n_mid, g->n_big, g->status);
         int flag = 0;
         if (cudaMemcpyAsync(&flag, g->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(CBFS_E_CUDA);
         if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);

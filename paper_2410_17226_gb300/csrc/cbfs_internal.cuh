@@ -9,21 +9,25 @@
 
 namespace cbfs {
 
-constexpr int kThreads = 256;                  // threads per CTA of every traversal kernel
+constexpr int kThreads = 256;       // threads per CTA of every traversal kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kTile = 1024;                    // frontier entries per phase-A tile
-constexpr int kPerThread = kTile / kThreads;   // entries per thread in a tile
-constexpr int kMaxSlots = 16;                  // clusters in flight per wave
-constexpr int kMaxRounds = 288;                // > 254 + 15 + 1: Delta < 255, offsets <= 15
-constexpr int64_t kBigDeg = 2048;              // push: longer lists are cut into pieces of this size
-constexpr int64_t kPullSmall = 32;             // pull: thread per vertex up to this degree
-constexpr int64_t kPullMid = 2048;             // pull: warp per vertex up to this degree, CTA above
+constexpr int kMaxSlots = 8;        // clusters in flight per wave: P in {1, 2, 4, 8}
+constexpr int kMaxRounds = 288;     // > 254 + 15 + 1: Delta < 255, offsets <= 15
+constexpr int64_t kBigDeg = 2048;   // push: longer lists are cut into pieces of this size
+constexpr int64_t kPullSmall = 32;  // pull: thread per vertex up to this degree
+constexpr int64_t kPullMid = 2048;  // pull: warp per vertex up to this degree, CTA above
+constexpr int kTileMin = kThreads;  // smallest phase-A tile (P >= 4)
+constexpr int kTileMax = 4 * kThreads;
 
-// One cluster in flight.  va[v] = {visit, acc}: visit = sources seen at rounds
-// <= the current one (Sseen of Algorithm 1), acc = sources pushed to v for
-// the next round and not yet consumed (the part of Snext not in Sseen).
+// Phase-A tiling for P clusters in flight: entries per thread and per tile.
+template <int P>
+struct Geo {
+    static constexpr int kEpt = P >= 4 ? 1 : 4 / P;
+    static constexpr int kTile = kThreads * kEpt;
+};
+
+// One cluster in flight: where its outputs go.
 struct SlotDesc {
-    ulonglong2* va;
     uint8_t* dist;    // output Delta_v, doubles as the "first round" state
     uint64_t* masks;  // output S_v[0..d-1]
     uint64_t all;     // the k low bits
@@ -33,8 +37,8 @@ struct SlotDesc {
 
 // Per-round control block, zeroed at the start of every wave.
 struct RoundCtl {
-    unsigned long long qlen;   // queue entries of F_i (appended during round i-1)
-    unsigned long long nf;     // entries that carried new sources (|F_i| over all slots)
+    unsigned long long qlen;   // queue entries (vertices) of F_i, appended during round i-1
+    unsigned long long nf;     // entries that carried new sources in some slot
     unsigned long long sdeg;   // sum of deg(u) over those entries
     unsigned int npieces;      // big-list pieces written by phase A
     unsigned int nbig;         // big-list entries written by phase A
@@ -49,29 +53,37 @@ struct RoundCtl {
 struct BigEntry {
     int64_t ost;  // off[u]
     int64_t deg;
-    uint64_t fw;  // the sources new at u this round
-    int32_t slot;
-    int32_t pad;
 };
 
 // Everything a traversal kernel needs, passed by value.
+//
+// Vertex-major state of the P clusters in flight:
+//   vis[v*P + s] = sources of slot s seen at rounds <= the current one
+//                  (Sseen of Algorithm 1);
+//   acc[v*P + s] = sources pushed to v for the next round and not yet
+//                  consumed (the part of Snext not in Sseen).
+// One adjacency scan and one gathered vis block serve all P clusters.
 struct Wave {
     int64_t n, nnz;
     const int64_t* off;
     const int32_t* adj;
     int d;
-    int nslots;
+    int P;                  // slots per vertex block (template P of the phase kernels)
+    int nslots;             // clusters in this wave (<= P)
     const SlotDesc* slots;  // device [nslots]
-    uint64_t* q0;           // frontier queues, entry = slot << 32 | v
-    uint64_t* q1;
+    uint64_t* vis;          // [n][P]
+    uint64_t* acc;          // [n][P]
+    uint32_t* rq;           // [n] queue claim stamps: F_i holds v iff rq[v] was set to i+1
+    uint32_t* q0;           // frontier queues of vertex ids
+    uint32_t* q1;
     RoundCtl* ctl;          // [kMaxRounds]
     uint32_t* t_pre;        // tile lists (compacted per tile): tile-local arc prefix
     int64_t* t_ost;         //   off[u]
-    uint64_t* t_fw;         //   new sources of u
-    uint8_t* t_slot;        //   slot
+    uint64_t* t_fw;         //   [entry][P] sources new at u this round
     uint32_t* tile_cnt;     // entries per tile
     uint32_t* tile_arcs;    // arcs per tile
     BigEntry* big;
+    uint64_t* big_fw;       // [entry][P]
     uint32_t* piece_ent;    // piece p covers arcs [piece_no*kBigDeg, ...) of big[piece_ent]
     uint32_t* piece_no;
     const int32_t* pl_small;  // pull lists: vertices by degree class, ascending ids
@@ -82,13 +94,31 @@ struct Wave {
     float alpha;            // pull threshold factor (<= 0: push only)
 };
 
+// Scratch capacities for n vertices and P slots (entries of each array).
+struct ScratchSizes {
+    int64_t state, queue, list, tiles;
+};
+inline ScratchSizes scratch_sizes(int64_t n, int P) {
+    ScratchSizes z;
+    z.state = n * P;
+    z.queue = n;
+    z.list = n + kTileMax;                   // tile slots: ntiles * tile <= n + tile - 1
+    z.tiles = (n + kTileMin - 1) / kTileMin + 1;
+    return z;
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
 // Traversal kernels (cbfs_core.cu).  seeds[i] = slot << 40 | j << 32 | vertex.
 __global__ void k_seed(Wave w, const uint64_t* seeds, int count);
 __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count);
+template <int P>
 __global__ void k_phase_a(Wave w, int round);
+template <int P>
 __global__ void k_phase_b(Wave w, int round);
+
+// Launches phase A and phase B of one round for w.P (1, 2, 4 or 8).
+cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which /*0 = A, 1 = B*/);
 
 }  // namespace cbfs
 

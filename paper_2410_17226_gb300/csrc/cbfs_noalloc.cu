@@ -27,26 +27,28 @@ namespace {
 
 constexpr int64_t kNoAllocMaxN = (int64_t)1 << 17;    // 131,072 vertices
 constexpr int64_t kNoAllocMaxNnz = (int64_t)1 << 22;  // 4,194,304 arcs
-constexpr int64_t kTilesMax = (kNoAllocMaxN + kTile - 1) / kTile;
-constexpr int64_t kTileSlots = kTilesMax * kTile;
+constexpr int64_t kListMax = kNoAllocMaxN + kTileMax;
+constexpr int64_t kTilesMax = (kNoAllocMaxN + kTileMin - 1) / kTileMin + 1;
 constexpr int64_t kBigMax = kNoAllocMaxNnz / (kBigDeg + 1) + 1;      // vertices of degree > kBigDeg
 constexpr int64_t kPiecesMax = kNoAllocMaxNnz / kBigDeg + kBigMax;   // their kBigDeg-arc pieces
 constexpr int kMaxDevices = 64;
 
 constexpr int64_t al256(int64_t x) { return (x + 255) / 256 * 256; }
 
-// byte offsets of the pieces of the scratch array
-constexpr int64_t kOffVa = 0;
-constexpr int64_t kOffQ0 = kOffVa + al256(16 * kNoAllocMaxN);
-constexpr int64_t kOffQ1 = kOffQ0 + al256(8 * kNoAllocMaxN);
-constexpr int64_t kOffPre = kOffQ1 + al256(8 * kNoAllocMaxN);
-constexpr int64_t kOffOst = kOffPre + al256(4 * kTileSlots);
-constexpr int64_t kOffFw = kOffOst + al256(8 * kTileSlots);
-constexpr int64_t kOffSlotIdx = kOffFw + al256(8 * kTileSlots);
-constexpr int64_t kOffTileCnt = kOffSlotIdx + al256(kTileSlots);
+// byte offsets of the pieces of the scratch array (one cluster in flight)
+constexpr int64_t kOffVis = 0;
+constexpr int64_t kOffAcc = kOffVis + al256(8 * kNoAllocMaxN);
+constexpr int64_t kOffRq = kOffAcc + al256(8 * kNoAllocMaxN);
+constexpr int64_t kOffQ0 = kOffRq + al256(4 * kNoAllocMaxN);
+constexpr int64_t kOffQ1 = kOffQ0 + al256(4 * kNoAllocMaxN);
+constexpr int64_t kOffPre = kOffQ1 + al256(4 * kNoAllocMaxN);
+constexpr int64_t kOffOst = kOffPre + al256(4 * kListMax);
+constexpr int64_t kOffFw = kOffOst + al256(8 * kListMax);
+constexpr int64_t kOffTileCnt = kOffFw + al256(8 * kListMax);
 constexpr int64_t kOffTileArcs = kOffTileCnt + al256(4 * kTilesMax);
 constexpr int64_t kOffBig = kOffTileArcs + al256(4 * kTilesMax);
-constexpr int64_t kOffPieceEnt = kOffBig + al256((int64_t)sizeof(BigEntry) * kBigMax);
+constexpr int64_t kOffBigFw = kOffBig + al256((int64_t)sizeof(BigEntry) * kBigMax);
+constexpr int64_t kOffPieceEnt = kOffBigFw + al256(8 * kBigMax);
 constexpr int64_t kOffPieceNo = kOffPieceEnt + al256(4 * kPiecesMax);
 constexpr int64_t kOffCtl = kOffPieceNo + al256(4 * kPiecesMax);
 constexpr int64_t kOffSlots = kOffCtl + al256((int64_t)sizeof(RoundCtl) * kMaxRounds);
@@ -109,18 +111,22 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     w.off = off;
     w.adj = adj;
     w.d = d;
+    w.P = 1;
     w.nslots = 1;
     w.slots = reinterpret_cast<const SlotDesc*>(base + kOffSlots);
-    w.q0 = reinterpret_cast<uint64_t*>(base + kOffQ0);
-    w.q1 = reinterpret_cast<uint64_t*>(base + kOffQ1);
+    w.vis = reinterpret_cast<uint64_t*>(base + kOffVis);
+    w.acc = reinterpret_cast<uint64_t*>(base + kOffAcc);
+    w.rq = reinterpret_cast<uint32_t*>(base + kOffRq);
+    w.q0 = reinterpret_cast<uint32_t*>(base + kOffQ0);
+    w.q1 = reinterpret_cast<uint32_t*>(base + kOffQ1);
     w.ctl = reinterpret_cast<RoundCtl*>(base + kOffCtl);
     w.t_pre = reinterpret_cast<uint32_t*>(base + kOffPre);
     w.t_ost = reinterpret_cast<int64_t*>(base + kOffOst);
     w.t_fw = reinterpret_cast<uint64_t*>(base + kOffFw);
-    w.t_slot = base + kOffSlotIdx;
     w.tile_cnt = reinterpret_cast<uint32_t*>(base + kOffTileCnt);
     w.tile_arcs = reinterpret_cast<uint32_t*>(base + kOffTileArcs);
     w.big = reinterpret_cast<BigEntry*>(base + kOffBig);
+    w.big_fw = reinterpret_cast<uint64_t*>(base + kOffBigFw);
     w.piece_ent = reinterpret_cast<uint32_t*>(base + kOffPieceEnt);
     w.piece_no = reinterpret_cast<uint32_t*>(base + kOffPieceNo);
     w.status = reinterpret_cast<int*>(base + kOffStatus);
@@ -128,7 +134,6 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
 
     SlotDesc sd;
     memset(&sd, 0, sizeof(sd));
-    sd.va = reinterpret_cast<ulonglong2*>(base + kOffVa);
     sd.dist = dist;
     sd.masks = d ? masks : nullptr;
     sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
@@ -147,7 +152,9 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     NA_CK(cudaMemcpyAsync(base + kOffSlots, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
     NA_CK(cudaMemcpyAsync(d_seeds, seeds, sizeof(uint64_t) * k, cudaMemcpyHostToDevice, st));
     // everything the traversal expects to start at zero (the array keeps the last call's data)
-    NA_CK(cudaMemsetAsync(sd.va, 0, 16 * (size_t)n, st));
+    NA_CK(cudaMemsetAsync(w.vis, 0, 8 * (size_t)n, st));
+    NA_CK(cudaMemsetAsync(w.acc, 0, 8 * (size_t)n, st));
+    NA_CK(cudaMemsetAsync(w.rq, 0, 4 * (size_t)n, st));
     NA_CK(cudaMemsetAsync(w.ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
     NA_CK(cudaMemsetAsync(w.status, 0, sizeof(int), st));
     NA_CK(cudaMemsetAsync(dist, 0xFF, (size_t)n, st));
@@ -156,9 +163,8 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     NA_CK(cudaGetLastError());
     bool done = false;
     for (int r = 0; r < kMaxRounds - 1; ++r) {
-        k_phase_a<<<grid, kThreads, 0, st>>>(w, r);
-        k_phase_b<<<grid, kThreads, 0, st>>>(w, r);
-        NA_CK(cudaGetLastError());
+        NA_CK(launch_round(w, r, grid, st, 0));
+        NA_CK(launch_round(w, r, grid, st, 1));
         unsigned long long qn = 0;
         NA_CK(cudaMemcpyAsync(&qn, &w.ctl[r + 1].qlen, sizeof(qn), cudaMemcpyDeviceToHost, st));
         NA_CK(cudaStreamSynchronize(st));
