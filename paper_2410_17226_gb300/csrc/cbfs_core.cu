@@ -325,20 +325,21 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             store_words<P>(w.vis + (size_t)u * P, vs);
             zero_words<P>(w.acc + (size_t)u * P);
             if (!any) continue;
+            const uint32_t o = w.perm ? (uint32_t)w.perm[u] : u;  // caller's id of u
 #pragma unroll
             for (int s = 0; s < P; ++s) {
                 if (!fw[r][s]) continue;
                 const SlotDesc& S = ss[s];
-                const uint8_t dd = S.dist[u];
+                const uint8_t dd = S.dist[o];
                 int j;
                 if (dd == 0xFF) {
                     if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
-                    else S.dist[u] = (uint8_t)round;
+                    else S.dist[o] = (uint8_t)round;
                     j = 0;
                 } else {
                     j = round - (int)dd;
                 }
-                if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = fw[r][s];
+                if (j < w.d) S.masks[(size_t)j * (size_t)w.n + o] = fw[r][s];
                 else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
                 my_active |= 1u << s;
             }
@@ -677,8 +678,12 @@ __global__ void k_output_stats(int64_t n, int d, const int64_t* off, const uint8
 
 struct cbfs_graph_s {
     int64_t n = 0, nnz = 0;
-    int64_t* off = nullptr;
-    int32_t* adj = nullptr;
+    int64_t* off = nullptr;    // caller's CSR offsets (kept for output statistics)
+    int32_t* adj = nullptr;    // caller's adjacency (freed once relabelled)
+    int64_t* off_r = nullptr;  // relabelled CSR the traversal runs on
+    int32_t* adj_r = nullptr;
+    int32_t* perm = nullptr;   // rank -> caller's id
+    std::vector<int32_t> iperm;  // caller's id -> rank (host, for the sources)
     int32_t* pl = nullptr;  // pull lists: small | mid | big
     int64_t n_small = 0, n_mid = 0, n_big = 0;
     int64_t big_vertices = 0, big_pieces = 0;
@@ -930,7 +935,7 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
                 sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
                 sd.cluster = c;
                 for (int j = 0; j < k; ++j)
-                    g->h_seeds[ns++] = ((uint64_t)s << 40) | ((uint64_t)j << 32) | (uint32_t)src[coff[c] + j];
+                    g->h_seeds[ns++] = ((uint64_t)s << 40) | ((uint64_t)j << 32) | (uint32_t)g->iperm[src[coff[c] + j]];
             }
             g->h_slots[(size_t)wv * P + s] = sd;
         }
@@ -945,8 +950,9 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     memset(&w, 0, sizeof(w));
     w.n = n;
     w.nnz = g->nnz;
-    w.off = g->off;
-    w.adj = g->adj;
+    w.off = g->off_r;
+    w.adj = g->adj_r;
+    w.perm = g->perm;
     w.d = d;
     w.P = P;
     w.vis = g->vis;
@@ -1085,7 +1091,7 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     if (nnz > 0 && cudaMemcpyAsync(g->adj, adj, sizeof(int32_t) * (size_t)nnz,
                                    inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess)
         return fail(CBFS_E_CUDA);
-    // degree classes for pull and validation, capacity of the push big list
+    // degree classes (caller's ids) for validation, capacity of the push big list
     std::vector<int32_t> ls, lm, lb;
     for (int64_t v = 0; v < n; ++v) {
         const int64_t dg = h_off[v + 1] - h_off[v];
@@ -1101,30 +1107,74 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     g->n_small = (int64_t)ls.size();
     g->n_mid = (int64_t)lm.size();
     g->n_big = (int64_t)lb.size();
-    rc = dev_alloc(&g->pl, g->n_small + g->n_mid + g->n_big);
+    const int64_t nlist = g->n_small + g->n_mid + g->n_big;
+    rc = dev_alloc(&g->pl, nlist);
     if (rc) return fail(rc);
-    if (g->n_small) cudaMemcpyAsync(g->pl, ls.data(), sizeof(int32_t) * ls.size(), cudaMemcpyHostToDevice, st);
-    if (g->n_mid) cudaMemcpyAsync(g->pl + g->n_small, lm.data(), sizeof(int32_t) * lm.size(), cudaMemcpyHostToDevice, st);
-    if (g->n_big)
-        cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, lb.data(), sizeof(int32_t) * lb.size(), cudaMemcpyHostToDevice, st);
     int sms = 0, occ = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    sms = std::max(1, sms);
     const void* kb[4] = {(const void*)k_phase_b<1>, (const void*)k_phase_b<2>, (const void*)k_phase_b<4>,
                          (const void*)k_phase_b<8>};
     for (int i = 0; i < 4; ++i) {
         occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb[i], kThreads, 0);
-        g->grid_p[i] = std::max(1, sms) * std::max(1, std::min(occ, 8));
+        g->grid_p[i] = sms * std::max(1, std::min(occ, 8));
     }
     if (validate && n > 0) {
+        if (g->n_small) cudaMemcpyAsync(g->pl, ls.data(), sizeof(int32_t) * ls.size(), cudaMemcpyHostToDevice, st);
+        if (g->n_mid) cudaMemcpyAsync(g->pl + g->n_small, lm.data(), sizeof(int32_t) * lm.size(), cudaMemcpyHostToDevice, st);
+        if (g->n_big)
+            cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, lb.data(), sizeof(int32_t) * lb.size(), cudaMemcpyHostToDevice, st);
         if (cudaMemsetAsync(g->status, 0, sizeof(int), st) != cudaSuccess) return fail(CBFS_E_CUDA);
-        k_validate<<<std::max(1, sms) * 8, kThreads, 0, st>>>(n, g->off, g->adj, g->pl, g->n_small, g->pl + g->n_small,
-                                                             g->n_mid, g->pl + g->n_small + g->n_mid, g->n_big, g->status);
+        k_validate<<<sms * 8, kThreads, 0, st>>>(n, g->off, g->adj, g->pl, g->n_small, g->pl + g->n_small, g->n_mid,
+                                                 g->pl + g->n_small + g->n_mid, g->n_big, g->status);
         int flag = 0;
         if (cudaMemcpyAsync(&flag, g->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(CBFS_E_CUDA);
         if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);
         if (flag) return fail(CBFS_E_GRAPH);
     }
+    // internal order: ranks by degree, hub-first adjacency (cbfs_relabel.cu)
+    std::vector<int32_t> perm;
+    std::vector<int64_t> off_r;
+    rank_order(n, h_off.data(), perm, g->iperm, off_r);
+    int32_t* d_iperm = nullptr;
+    rc = dev_alloc(&g->off_r, n + 1);
+    if (!rc) rc = dev_alloc(&g->adj_r, nnz);
+    if (!rc) rc = dev_alloc(&g->perm, n);
+    if (!rc) rc = dev_alloc(&d_iperm, n);
+    if (rc) {
+        dev_free(d_iperm);
+        return fail(rc);
+    }
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(g->off_r, off_r.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_iperm, g->iperm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && nnz > 0)
+            e = relabel_adjacency(n, g->n_big, g->n_mid, g->n_small, g->perm, d_iperm, g->off, g->adj, g->off_r, g->adj_r,
+                                  sms, st);
+    } else {
+        e = cudaMemsetAsync(g->off_r, 0, sizeof(int64_t), st);
+    }
+    // pull lists in rank space: the degree classes are consecutive rank ranges
+    std::vector<int32_t> ranks((size_t)nlist);
+    for (int64_t i = 0; i < nlist; ++i) ranks[(size_t)i] = (int32_t)i;
+    // order inside pl: small | mid | big, as the traversal expects
+    if (e == cudaSuccess && g->n_small)
+        e = cudaMemcpyAsync(g->pl, ranks.data() + g->n_big + g->n_mid, sizeof(int32_t) * (size_t)g->n_small,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && g->n_mid)
+        e = cudaMemcpyAsync(g->pl + g->n_small, ranks.data() + g->n_big, sizeof(int32_t) * (size_t)g->n_mid,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && g->n_big)
+        e = cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, ranks.data(), sizeof(int32_t) * (size_t)g->n_big,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(d_iperm);
+    if (e != cudaSuccess) return fail(CBFS_E_CUDA);
+    dev_free(g->adj);  // the caller's adjacency is no longer needed
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);
     if (cudaGetLastError() != cudaSuccess) return fail(CBFS_E_CUDA);
     *out = g;
@@ -1138,6 +1188,9 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     free_scratch(g);
     dev_free(g->off);
     dev_free(g->adj);
+    dev_free(g->off_r);
+    dev_free(g->adj_r);
+    dev_free(g->perm);
     dev_free(g->pl);
     dev_free(g->ctl);
     dev_free(g->status);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "cbfs.h"
 
 namespace cbfs {
@@ -90,6 +92,7 @@ struct Wave {
     const int32_t* pl_mid;
     const int32_t* pl_big;
     int64_t n_small, n_mid, n_big;
+    const int32_t* perm;    // internal vertex -> caller's id for the outputs (nullptr: identity)
     int* status;
     float alpha;            // pull threshold factor (<= 0: push only)
 };
@@ -116,6 +119,17 @@ template <int P>
 __global__ void k_phase_a(Wave w, int round);
 template <int P>
 __global__ void k_phase_b(Wave w, int round);
+
+// Internal vertex order (cbfs_relabel.cu): ranks by degree, highest first,
+// ties to the smaller id; perm[rank] = id, iperm[id] = rank, off_r = offsets
+// of the relabelled CSR.
+void rank_order(int64_t n, const int64_t* h_off, std::vector<int32_t>& perm, std::vector<int32_t>& iperm,
+                std::vector<int64_t>& off_r);
+// Writes the relabelled adjacency (ranks, hubs first) of the ranks
+// [0, n_big) (degree > kPullMid), then n_mid, then n_small vertices.
+cudaError_t relabel_adjacency(int64_t n, int64_t n_big, int64_t n_mid, int64_t n_small, const int32_t* d_perm,
+                              const int32_t* d_iperm, const int64_t* d_off, const int32_t* d_adj, const int64_t* d_off_r,
+                              int32_t* d_adj_r, int sms, cudaStream_t st);
 
 // Launches phase A and phase B of one round for w.P (1, 2, 4 or 8).
 cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which /*0 = A, 1 = B*/);
