@@ -64,11 +64,15 @@ typedef struct cbfs_labels_s* cbfs_labels_t;
 typedef struct cbfs_tune_s {
     /* Direction optimisation (Appendix A, EdgeMap): a round runs dense (pull)
        when |F| + sum_{u in F} deg(u) > pull_alpha * nnz * (clusters in flight);
-       < 0 disables pull.  0 = default (1/10, the paper's commented rule). */
+       < 0 disables pull.  0 = default (0.02; the paper's commented rule is 1/10). */
     float pull_alpha;
-    /* clusters traversed concurrently in one batched wave (1..16).  0 = default. */
+    /* clusters traversed concurrently in one batched wave; rounded down to a
+       power of two in 1..8.  0 = default (4). */
     int slots;
-    int reserved[6];
+    /* the vertex phase scans every vertex instead of the frontier queue when
+       |F| * dense_div > n.  0 = default (16); < 0 = never. */
+    int dense_div;
+    int reserved[5];
 } cbfs_tune_t;
 
 /* Work counters of one cluster's traversal (Theorem 1). */

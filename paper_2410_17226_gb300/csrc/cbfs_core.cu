@@ -152,14 +152,19 @@ __device__ __forceinline__ void zero_words(uint64_t* p) {
     store_words<P>(p, z);
 }
 
-// ORs the vis blocks of up to four neighbours adj[e .. min(e + 4 * step, o1))
-// taken every `step` arcs into acc; all four gathers are issued before any
+// ORs into acc the vis blocks of the frontier neighbours among up to four
+// arcs adj[e], adj[e + step], ... below o1; all gathers are issued before any
 // is used.
 template <int P>
-__device__ __forceinline__ void gather4(const Wave& w, int64_t e, int64_t step, int64_t o1, uint64_t (&acc)[P]) {
+__device__ __forceinline__ void gather4(const Wave& w, const uint32_t* fb, const int32_t* adj, int64_t e, int64_t step,
+                                        int64_t o1, uint64_t (&acc)[P]) {
     int32_t u[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) u[k] = (e + k * step < o1) ? w.adj[e + k * step] : -1;
+    for (int k = 0; k < 4; ++k) u[k] = (e + k * step < o1) ? adj[e + k * step] : -1;
+    // only frontier neighbours can carry sources v has not seen
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (u[k] >= 0 && !((fb[u[k] >> 5] >> (u[k] & 31)) & 1u)) u[k] = -1;
     uint64_t x[4][P];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -175,10 +180,28 @@ __device__ __forceinline__ void gather4(const Wave& w, int64_t e, int64_t step, 
         for (int s = 0; s < P; ++s) acc[s] |= x[k][s];
 }
 
+// Appends v to the next frontier and adds deg to its degree sum (the
+// direction decision of the next round); one atomic pair per warp.
+__device__ __forceinline__ void append_next(uint32_t* q, RoundCtl* cn, uint32_t v, uint32_t deg) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    // 32 degrees < 2^31 each: sum the high and low halves separately in 32 bits
+    const unsigned int hi = __reduce_add_sync(mask, deg >> 16);
+    const unsigned int lo = __reduce_add_sync(mask, deg & 0xFFFFu);
+    unsigned long long base = 0;
+    if (lane == leader) {
+        base = atomicAdd(&cn->qlen, (unsigned long long)__popc(mask));
+        atomicAdd(&cn->sdeg, ((unsigned long long)hi << 16) + (unsigned long long)lo);
+    }
+    base = __shfl_sync(mask, base, leader);
+    q[base + __popc(mask & ((1u << lane) - 1u))] = v;
+}
+
 // Push the new sources fw[0..P) of a frontier vertex along one arc to t.
 template <int P>
 __device__ __forceinline__ void push_arc(const Wave& w, const uint64_t* fw, uint32_t t, uint32_t stamp, uint32_t* qn,
-                                         unsigned long long* qlen_next) {
+                                         RoundCtl* cn) {
     uint64_t vs[P], b[P];
     load_words<P>(w.vis + (size_t)t * P, vs);  // vis is read-only in phase B
     uint64_t any = 0;
@@ -201,12 +224,15 @@ __device__ __forceinline__ void push_arc(const Wave& w, const uint64_t* fw, uint
         }
     }
     if (!claim) return;
-    if (P == 1 || atomicExch(w.rq + t, stamp) != stamp) append(qn, qlen_next, t);
+    if (P == 1 || atomicExch(w.rq + t, stamp) != stamp)
+        append_next(qn, cn, t, (uint32_t)(w.off[t + 1] - w.off[t]));
 }
 
+// Direction of a round (Algorithm "EdgeMap"): dense when the frontier and
+// its arcs are a large part of the graph.
 __device__ __forceinline__ bool decide_pull(const Wave& w, const RoundCtl* c) {
     if (!(w.alpha > 0.f)) return false;
-    const double work = (double)c->nf + (double)c->sdeg;
+    const double work = (double)c->qlen + (double)c->sdeg;
     return work > (double)w.alpha * (double)w.nnz;
 }
 
@@ -230,10 +256,12 @@ __device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], cons
     return um;
 }
 
-// Pull result of v: keep the new part as acc[v] and queue v.
+// Pull result of v: keep the new part as acc[v].  A pull round writes no
+// queue (the next vertex phase scans densely); it only counts the new
+// frontier and its arcs for the next direction decision.
 template <int P>
 __device__ __forceinline__ void pull_finish(const Wave& w, int32_t v, const uint64_t (&acc)[P], const uint64_t (&vs)[P],
-                                            uint32_t* qn, unsigned long long* qlen_next) {
+                                            uint32_t deg, unsigned long long& cnt, unsigned long long& sdeg) {
     uint64_t nw[P], any = 0;
 #pragma unroll
     for (int s = 0; s < P; ++s) {
@@ -242,7 +270,8 @@ __device__ __forceinline__ void pull_finish(const Wave& w, int32_t v, const uint
     }
     if (any) {
         store_words<P>(w.acc + (size_t)v * P, nw);
-        append(qn, qlen_next, (uint32_t)v);
+        cnt += 1;
+        sdeg += deg;
     }
 }
 
@@ -262,7 +291,10 @@ __global__ void k_seed(Wave w, const uint64_t* seeds, int count) {
         const int s = (int)((e >> 40) & 0xFF), j = (int)((e >> 32) & 0xFF);
         const uint32_t v = (uint32_t)e;
         w.acc[(size_t)v * w.P + s] = 1ull << j;  // (v, s) is unique within a wave
-        if (atomicExch(w.rq + v, 1u) != 1u) append(w.q0, &w.ctl[0].qlen, v);
+        if (atomicExch(w.rq + v, 1u) != 1u) {
+            append(w.q0, &w.ctl[0].qlen, v);
+            atomicAdd(&w.ctl[0].sdeg, (unsigned long long)(w.off[v + 1] - w.off[v]));
+        }
     }
 }
 
@@ -278,7 +310,11 @@ __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count) {
     }
 }
 
-// Phase A: the vertex phase of round `round` and the push work lists.
+// Phase A: the vertex phase of round `round`, the direction decision and,
+// for a push round, the push work lists.  A small frontier is read from the
+// queue; a large one (qlen * dense_div > n) by scanning every vertex in
+// internal order for a non-zero acc block, which streams instead of
+// gathering.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     constexpr int EPT = Geo<P>::kEpt;
@@ -290,12 +326,17 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     RoundCtl* c = w.ctl + round;
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
+    const bool pull = decide_pull(w, c);
+    const bool dense = c->dense || (w.dense_div > 0 && qlen * (unsigned long long)w.dense_div > (unsigned long long)w.n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->mode = pull ? 1 : 0;
     if (threadIdx.x < w.nslots) ss[threadIdx.x] = w.slots[threadIdx.x];
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
     const uint32_t* q = (round & 1) ? w.q1 : w.q0;
-    const unsigned long long ntiles = (qlen + TILE - 1) / TILE;
-    unsigned long long my_nf = 0, my_sdeg = 0;
+    uint32_t* fbw = (round & 1) ? w.fb1 : w.fb0;
+    const unsigned long long span = dense ? (unsigned long long)w.n : qlen;
+    const unsigned long long ntiles = (span + TILE - 1) / TILE;
+    unsigned long long my_nf = 0;
     unsigned int my_active = 0;
     for (unsigned long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         uint32_t keep[EPT], dg[EPT];
@@ -310,10 +351,14 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
 #pragma unroll
             for (int s = 0; s < P; ++s) fw[r][s] = 0;
             const unsigned long long idx = t * TILE + (unsigned long long)threadIdx.x * EPT + r;
-            if (idx >= qlen) continue;
-            const uint32_t u = q[idx];
+            if (idx >= span) continue;
+            const uint32_t u = dense ? (uint32_t)idx : q[idx];
             uint64_t a[P], vs[P];
             load_words<P>(w.acc + (size_t)u * P, a);
+            uint64_t anyacc = 0;
+#pragma unroll
+            for (int s = 0; s < P; ++s) anyacc |= a[s];
+            if (!anyacc) continue;  // not in F_round (dense scan), or nothing new
             load_words<P>(w.vis + (size_t)u * P, vs);
             uint64_t any = 0;
 #pragma unroll
@@ -325,28 +370,47 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             store_words<P>(w.vis + (size_t)u * P, vs);
             zero_words<P>(w.acc + (size_t)u * P);
             if (!any) continue;
-            const uint32_t o = w.perm ? (uint32_t)w.perm[u] : u;  // caller's id of u
+            atomicOr(fbw + (u >> 5), 1u << (u & 31));
+            if (w.dist_r) {
+                // the wave's internal rows of u
+                uint8_t* dr = w.dist_r + (size_t)u * P;
+                uint64_t* mr = w.masks_r + (size_t)u * w.d * P;
 #pragma unroll
-            for (int s = 0; s < P; ++s) {
-                if (!fw[r][s]) continue;
-                const SlotDesc& S = ss[s];
-                const uint8_t dd = S.dist[o];
+                for (int s = 0; s < P; ++s) {
+                    if (!fw[r][s]) continue;
+                    const uint8_t dd = dr[s];
+                    int j;
+                    if (dd == 0xFF) {
+                        if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
+                        else dr[s] = (uint8_t)round;
+                        j = 0;
+                    } else {
+                        j = round - (int)dd;
+                    }
+                    if (j < w.d) mr[(size_t)j * P + s] = fw[r][s];
+                    else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
+                    my_active |= 1u << s;
+                }
+            } else {
+                // direct: one cluster, caller's ids, caller's arrays
+                const SlotDesc& S = ss[0];
+                const uint8_t dd = S.dist[u];
                 int j;
                 if (dd == 0xFF) {
                     if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
-                    else S.dist[o] = (uint8_t)round;
+                    else S.dist[u] = (uint8_t)round;
                     j = 0;
                 } else {
                     j = round - (int)dd;
                 }
-                if (j < w.d) S.masks[(size_t)j * (size_t)w.n + o] = fw[r][s];
+                if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = fw[r][0];
                 else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
-                my_active |= 1u << s;
+                my_active |= 1u;
             }
+            my_nf += 1;
+            if (pull) continue;  // the dense edge phase needs no work lists
             const int64_t o0 = w.off[u], o1 = w.off[u + 1];
             const int64_t deg = o1 - o0;
-            my_nf += 1;
-            my_sdeg += (unsigned long long)deg;
             if (deg == 0) continue;
             if (deg > kBigDeg) {
                 // big list: one entry plus ceil(deg / kBigDeg) piece records
@@ -368,38 +432,37 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             cnt += 1;
             arcs += (uint32_t)deg;
         }
-        uint32_t ecnt, earcs, tcnt, tarcs;
-        block_scan2(cnt, arcs, ecnt, earcs, tcnt, tarcs, scan);
-        const unsigned long long base = t * TILE;
+        if (!pull) {
+            uint32_t ecnt, earcs, tcnt, tarcs;
+            block_scan2(cnt, arcs, ecnt, earcs, tcnt, tarcs, scan);
+            const unsigned long long base = t * TILE;
 #pragma unroll
-        for (int r = 0; r < EPT; ++r) {
-            if (!keep[r]) continue;
-            const unsigned long long pos = base + ecnt;
-            w.t_pre[pos] = earcs;
-            w.t_ost[pos] = ost[r];
-            store_words<P>(w.t_fw + pos * P, fw[r]);
-            ecnt += 1;
-            earcs += dg[r];
-        }
-        if (threadIdx.x == 0) {
-            w.tile_cnt[t] = tcnt;
-            w.tile_arcs[t] = tarcs;
+            for (int r = 0; r < EPT; ++r) {
+                if (!keep[r]) continue;
+                const unsigned long long pos = base + ecnt;
+                w.t_pre[pos] = earcs;
+                w.t_ost[pos] = ost[r];
+                store_words<P>(w.t_fw + pos * P, fw[r]);
+                ecnt += 1;
+                earcs += dg[r];
+            }
+            if (threadIdx.x == 0) {
+                w.tile_cnt[t] = tcnt;
+                w.tile_arcs[t] = tarcs;
+            }
         }
     }
-    // per-round totals for the direction decision
     const unsigned long long bnf = block_sum(my_nf, red);
-    const unsigned long long bsd = block_sum(my_sdeg, red);
     const unsigned int wa = __reduce_or_sync(0xffffffffu, my_active);
     if ((threadIdx.x & 31) == 0 && wa) atomicOr(&s_active, wa);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (bnf) atomicAdd(&c->nf, bnf);
-        if (bsd) atomicAdd(&c->sdeg, bsd);
         if (s_active) atomicOr(&c->slot_active, s_active);
     }
 }
 
-// Phase B: the edge phase of round `round`.
+// Phase B: the edge phase of round `round` in the direction phase A chose.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
     constexpr int TILE = Geo<P>::kTile;
@@ -409,16 +472,24 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
     __shared__ uint64_t sall[P];
     __shared__ unsigned int s_work;
     __shared__ uint64_t sor[kWarps][P];
+    __shared__ int32_t sadj[kWarps][32 * kPullSmall];
     RoundCtl* c = w.ctl + round;
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
     if (threadIdx.x < P) sall[threadIdx.x] = (int)threadIdx.x < w.nslots ? w.slots[threadIdx.x].all : 0ull;
     __syncthreads();
     uint32_t* qn = (round & 1) ? w.q0 : w.q1;
-    unsigned long long* qlen_next = &w.ctl[round + 1].qlen;
+    RoundCtl* cn = w.ctl + round + 1;
     const uint32_t stamp = (uint32_t)round + 2;  // F_{round+1}
-    const bool pull = decide_pull(w, c);
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->mode = pull ? 1 : 0;
+    const bool pull = c->mode != 0;
+    {
+        // F_{round+1}'s bitmap was last read in round - 1: clear it for phase A of round + 1
+        uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
+        const int64_t words = (w.n + 31) / 32;
+        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads)
+            fbn[i] = 0u;
+    }
+    const uint32_t* fb = (round & 1) ? w.fb1 : w.fb0;
 
     if (!pull) {
         // big-list pieces: kBigDeg consecutive arcs of one hub per CTA step
@@ -434,11 +505,13 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
             const int64_t a0 = (int64_t)w.piece_no[p] * kBigDeg;
             const int64_t a1 = min(be.deg, a0 + kBigDeg);
             for (int64_t a = a0 + threadIdx.x; a < a1; a += kThreads)
-                push_arc<P>(w, sfw, (uint32_t)w.adj[be.ost + a], stamp, qn, qlen_next);
+                push_arc<P>(w, sfw, (uint32_t)w.adj[be.ost + a], stamp, qn, cn);
             __syncthreads();
         }
         // tiles: entries of degree <= kBigDeg, arcs spread over the threads
-        const unsigned long long ntiles = (qlen + TILE - 1) / TILE;
+        const bool dense = c->dense || (w.dense_div > 0 && qlen * (unsigned long long)w.dense_div > (unsigned long long)w.n);
+        const unsigned long long span = dense ? (unsigned long long)w.n : qlen;
+        const unsigned long long ntiles = (span + TILE - 1) / TILE;
         for (;;) {
             if (threadIdx.x == 0) s_work = atomicAdd(&c->tile_ctr, 1u);
             __syncthreads();
@@ -467,7 +540,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
                         if (spre[mid] <= a) lo = mid;
                         else hi = mid - 1;
                     }
-                    push_arc<P>(w, sfw + lo * P, (uint32_t)w.adj[sost[lo] + (a - spre[lo])], stamp, qn, qlen_next);
+                    push_arc<P>(w, sfw + lo * P, (uint32_t)w.adj[sost[lo] + (a - spre[lo])], stamp, qn, cn);
                 }
                 __syncthreads();
             }
@@ -477,6 +550,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
 
     // ---- pull: dense pass over every vertex that can still gain sources
     const unsigned int active = c->slot_active;
+    unsigned long long my_cnt = 0, my_sdeg = 0;
     uint64_t all[P];
 #pragma unroll
     for (int s = 0; s < P; ++s) all[s] = sall[s];
@@ -492,7 +566,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] = 0;
         for (int64_t b0 = o0; b0 < o1; b0 += 4 * kThreads) {
-            gather4<P>(w, b0 + threadIdx.x, kThreads, o1, acc);
+            gather4<P>(w, fb, w.adj, b0 + threadIdx.x, kThreads, o1, acc);
 #pragma unroll
             for (int s = 0; s < P; ++s) {
                 const uint64_t wa = warp_or(acc[s]);
@@ -510,35 +584,15 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
             __syncthreads();
             if (missing_bits<P>(acc, vs, all, um) == 0) break;
         }
-        if (threadIdx.x == 0) pull_finish<P>(w, v, acc, vs, qn, qlen_next);
+        if (threadIdx.x == 0) pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
     }
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nw_total = ((int64_t)gridDim.x * kThreads) >> 5;
     // warp per mid-degree vertex
-    {
-        const int lane = threadIdx.x & 31;
-        const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-        const int64_t nw_total = ((int64_t)gridDim.x * kThreads) >> 5;
-        for (int64_t i = gw; i < w.n_mid; i += nw_total) {
-            const int32_t v = w.pl_mid[i];
-            uint64_t vs[P];
-            load_words<P>(w.vis + (size_t)v * P, vs);
-            const unsigned int um = unfinished<P>(vs, all, active);
-            if (!um) continue;
-            const int64_t o0 = w.off[v], o1 = w.off[v + 1];
-            uint64_t acc[P];
-#pragma unroll
-            for (int s = 0; s < P; ++s) acc[s] = 0;
-            for (int64_t b0 = o0; b0 < o1; b0 += 128) {
-                gather4<P>(w, b0 + lane, 32, o1, acc);
-#pragma unroll
-                for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
-                if (missing_bits<P>(acc, vs, all, um) == 0) break;
-            }
-            if (lane == 0) pull_finish<P>(w, v, acc, vs, qn, qlen_next);
-        }
-    }
-    // thread per low-degree vertex
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < w.n_small; i += (int64_t)gridDim.x * kThreads) {
-        const int32_t v = w.pl_small[i];
+    for (int64_t i = gw; i < w.n_mid; i += nw_total) {
+        const int32_t v = w.pl_mid[i];
         uint64_t vs[P];
         load_words<P>(w.vis + (size_t)v * P, vs);
         const unsigned int um = unfinished<P>(vs, all, active);
@@ -547,11 +601,76 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
         uint64_t acc[P];
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] = 0;
-        for (int64_t e = o0; e < o1; e += 4) {
-            gather4<P>(w, e, 1, o1, acc);
+        for (int64_t b0 = o0; b0 < o1; b0 += 128) {
+            gather4<P>(w, fb, w.adj, b0 + lane, 32, o1, acc);
+#pragma unroll
+            for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
             if (missing_bits<P>(acc, vs, all, um) == 0) break;
         }
-        pull_finish<P>(w, v, acc, vs, qn, qlen_next);
+        if (lane == 0) pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
+    }
+    // low-degree vertices: a warp takes 32 consecutive ones, whose lists are
+    // consecutive in the internal order, stages them in shared memory with
+    // coalesced loads, then each lane scans its own list
+    int32_t* wadj = sadj[wib];
+    for (int64_t g0 = gw * 32; g0 < w.n_small; g0 += nw_total * 32) {
+        const int64_t i = g0 + lane;
+        const bool has = i < w.n_small;
+        const int32_t v = has ? w.pl_small[i] : 0;
+        const int64_t o0 = has ? w.off[v] : 0, o1 = has ? w.off[v + 1] : 0;
+        const int last = (int)((w.n_small - 1 - g0) < 31 ? (w.n_small - 1 - g0) : 31);
+        const int64_t lo = __shfl_sync(0xffffffffu, o0, 0);
+        const int64_t hi = __shfl_sync(0xffffffffu, o1, last);
+        for (int64_t x = lo + lane; x < hi; x += 32) wadj[x - lo] = w.adj[x];
+        __syncwarp();
+        if (has) {
+            uint64_t vs[P];
+            load_words<P>(w.vis + (size_t)v * P, vs);
+            const unsigned int um = unfinished<P>(vs, all, active);
+            if (um) {
+                uint64_t acc[P];
+#pragma unroll
+                for (int s = 0; s < P; ++s) acc[s] = 0;
+                for (int64_t e = o0; e < o1; e += 4) {
+                    gather4<P>(w, fb, wadj - lo, e, 1, o1, acc);
+                    if (missing_bits<P>(acc, vs, all, um) == 0) break;
+                }
+                pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
+            }
+        }
+        __syncwarp();
+    }
+    // publish the next frontier's size and arcs: one atomic pair per CTA
+    __shared__ unsigned long long red[kWarps];
+    const unsigned long long bc = block_sum(my_cnt, red);
+    const unsigned long long bs = block_sum(my_sdeg, red);
+    if (threadIdx.x == 0) {
+        if (bc) atomicAdd(&cn->qlen, bc);
+        if (bs) atomicAdd(&cn->sdeg, bs);
+        if (blockIdx.x == 0) cn->dense = 1;
+    }
+}
+
+// Writes the wave's internal rows to the caller's outputs: caller vertex v
+// reads the row of its internal rank (coalesced writes per cluster).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm) {
+    __shared__ SlotDesc ss[P];
+    if (threadIdx.x < w.nslots) ss[threadIdx.x] = w.slots[threadIdx.x];
+    __syncthreads();
+    const int d = w.d;
+    for (int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x; v < w.n; v += (int64_t)gridDim.x * kThreads) {
+        const int64_t r = iperm ? iperm[v] : v;
+        const uint8_t* dr = w.dist_r + (size_t)r * P;
+        const uint64_t* mr = w.masks_r + (size_t)r * d * P;
+        for (int s = 0; s < w.nslots; ++s) ss[s].dist[v] = dr[s];
+        for (int j = 0; j < d; ++j) {
+            uint64_t m[P];
+            load_words<P>(mr + (size_t)j * P, m);
+#pragma unroll
+            for (int s = 0; s < P; ++s)
+                if (s < w.nslots) ss[s].masks[(size_t)j * (size_t)w.n + v] = m[s];
+        }
     }
 }
 
@@ -563,13 +682,18 @@ template __global__ void k_phase_b<1>(Wave, int);
 template __global__ void k_phase_b<2>(Wave, int);
 template __global__ void k_phase_b<4>(Wave, int);
 template __global__ void k_phase_b<8>(Wave, int);
+template __global__ void k_emit<1>(Wave, const int32_t*);
+template __global__ void k_emit<2>(Wave, const int32_t*);
+template __global__ void k_emit<4>(Wave, const int32_t*);
+template __global__ void k_emit<8>(Wave, const int32_t*);
 
-cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which) {
+cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which, const int32_t* iperm) {
     switch (w.P) {
 #define CBFS_CASE(PP)                                                       \
     case PP:                                                                \
         if (which == 0) k_phase_a<PP><<<grid, kThreads, 0, st>>>(w, round); \
-        else k_phase_b<PP><<<grid, kThreads, 0, st>>>(w, round);            \
+        else if (which == 1) k_phase_b<PP><<<grid, kThreads, 0, st>>>(w, round); \
+        else k_emit<PP><<<grid, kThreads, 0, st>>>(w, iperm);               \
         break;
         CBFS_CASE(1)
         CBFS_CASE(2)
@@ -683,7 +807,11 @@ struct cbfs_graph_s {
     int64_t* off_r = nullptr;  // relabelled CSR the traversal runs on
     int32_t* adj_r = nullptr;
     int32_t* perm = nullptr;   // rank -> caller's id
+    int32_t* iperm_d = nullptr;  // caller's id -> rank (device, for the output emit)
     std::vector<int32_t> iperm;  // caller's id -> rank (host, for the sources)
+    uint8_t* dist_r = nullptr;   // internal output rows of a wave
+    uint64_t* masks_r = nullptr;
+    int64_t masks_r_cap = 0;
     int32_t* pl = nullptr;  // pull lists: small | mid | big
     int64_t n_small = 0, n_mid = 0, n_big = 0;
     int64_t big_vertices = 0, big_pieces = 0;
@@ -696,6 +824,7 @@ struct cbfs_graph_s {
     uint32_t* rq = nullptr;
     uint32_t* q0 = nullptr;
     uint32_t* q1 = nullptr;
+    uint32_t* fb = nullptr;  // two frontier bitmaps
     uint32_t* t_pre = nullptr;
     int64_t* t_ost = nullptr;
     uint64_t* t_fw = nullptr;
@@ -769,6 +898,8 @@ void free_scratch(cbfs_graph_s* g) {
     dev_free(g->rq);
     dev_free(g->q0);
     dev_free(g->q1);
+    dev_free(g->fb);
+    dev_free(g->dist_r);
     dev_free(g->t_pre);
     dev_free(g->t_ost);
     dev_free(g->t_fw);
@@ -791,6 +922,8 @@ int ensure_scratch(cbfs_graph_s* g, int P) {
     if (!rc) rc = dev_alloc(&g->rq, z.queue);
     if (!rc) rc = dev_alloc(&g->q0, z.queue);
     if (!rc) rc = dev_alloc(&g->q1, z.queue);
+    if (!rc) rc = dev_alloc(&g->fb, 2 * z.bitmap);
+    if (!rc) rc = dev_alloc(&g->dist_r, z.state);
     if (!rc) rc = dev_alloc(&g->t_pre, z.list);
     if (!rc) rc = dev_alloc(&g->t_ost, z.list);
     if (!rc) rc = dev_alloc(&g->t_fw, z.list * P);
@@ -908,7 +1041,10 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     const int P = slots_for(tune, C);
     float alpha = 0.02f;
     if (tune && tune->pull_alpha != 0.f) alpha = tune->pull_alpha;
+    int dense_div = 16;
+    if (tune && tune->dense_div != 0) dense_div = tune->dense_div < 0 ? 0 : tune->dense_div;
     rc = ensure_scratch(g, P);
+    if (!rc) rc = ensure_dev(&g->masks_r, &g->masks_r_cap, std::max<int64_t>(1, g->n * d * P));
     if (rc) return rc;
     const int grid = g->grid_p[P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3];
     const int nwaves = (C + P - 1) / P;
@@ -960,6 +1096,9 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     w.rq = g->rq;
     w.q0 = g->q0;
     w.q1 = g->q1;
+    const int64_t bm_words = scratch_sizes(n, P).bitmap;
+    w.fb0 = g->fb;
+    w.fb1 = g->fb + bm_words;
     w.ctl = g->ctl;
     w.t_pre = g->t_pre;
     w.t_ost = g->t_ost;
@@ -978,6 +1117,9 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     w.n_big = g->n_big;
     w.status = g->status;
     w.alpha = alpha;
+    w.dist_r = g->dist_r;
+    w.masks_r = g->masks_r;
+    w.dense_div = dense_div;
 
     for (int wv = 0; wv < nwaves; ++wv) {
         const int c0 = wv * P;
@@ -987,8 +1129,9 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
         CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->rq, 0, sizeof(uint32_t) * (size_t)n, st));
-        CK(cudaMemsetAsync(dist + (size_t)c0 * (size_t)n, 0xFF, (size_t)nsl * (size_t)n, st));
-        if (d) CK(cudaMemsetAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, 0, sizeof(uint64_t) * (size_t)nsl * d * n, st));
+        CK(cudaMemsetAsync(g->fb, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, st));
+        CK(cudaMemsetAsync(g->dist_r, 0xFF, (size_t)P * (size_t)n, st));
+        if (d) CK(cudaMemsetAsync(g->masks_r, 0, sizeof(uint64_t) * (size_t)P * d * n, st));
         CK(cudaMemsetAsync(g->ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
         const int cnt = (int)(wave_seed_off[wv + 1] - wave_seed_off[wv]);
         int ev = prof_begin(g, 0, st);
@@ -1014,6 +1157,9 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
             prof_collect(g);
             return CBFS_E_DEPTH;
         }
+        ev = prof_begin(g, 0, st);
+        CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
+        prof_end(g, ev, st);
         ev = prof_begin(g, 0, st);
         k_check_sources<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
         prof_end(g, ev, st);
@@ -1172,7 +1318,7 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
         e = cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, ranks.data(), sizeof(int32_t) * (size_t)g->n_big,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    dev_free(d_iperm);
+    g->iperm_d = d_iperm;
     if (e != cudaSuccess) return fail(CBFS_E_CUDA);
     dev_free(g->adj);  // the caller's adjacency is no longer needed
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);
@@ -1191,6 +1337,8 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->off_r);
     dev_free(g->adj_r);
     dev_free(g->perm);
+    dev_free(g->iperm_d);
+    dev_free(g->masks_r);
     dev_free(g->pl);
     dev_free(g->ctl);
     dev_free(g->status);

@@ -40,15 +40,17 @@ struct SlotDesc {
 // Per-round control block, zeroed at the start of every wave.
 struct RoundCtl {
     unsigned long long qlen;   // queue entries (vertices) of F_i, appended during round i-1
-    unsigned long long nf;     // entries that carried new sources in some slot
-    unsigned long long sdeg;   // sum of deg(u) over those entries
+    unsigned long long nf;     // entries that carried new sources in some slot (phase A)
+    unsigned long long sdeg;   // sum of deg(u) over the queue entries, added by their producers
     unsigned int npieces;      // big-list pieces written by phase A
     unsigned int nbig;         // big-list entries written by phase A
     unsigned int tile_ctr;     // phase-B work counters
     unsigned int piece_ctr;
     unsigned int slot_active;  // bit s: slot s has a non-empty frontier this round
-    int mode;                  // 0 push, 1 pull (recorded by phase B)
-    unsigned int pad[2];
+    int mode;                  // 0 push, 1 pull: decided by phase A from qlen and sdeg
+    int dense;                 // 1: F_i was produced by a pull round and is not in the queue;
+                               //    phase A finds it by scanning every vertex's acc block
+    unsigned int pad;
 };
 
 // A frontier vertex whose list is longer than kBigDeg (push mode).
@@ -78,6 +80,8 @@ struct Wave {
     uint32_t* rq;           // [n] queue claim stamps: F_i holds v iff rq[v] was set to i+1
     uint32_t* q0;           // frontier queues of vertex ids
     uint32_t* q1;
+    uint32_t* fb0;          // frontier bitmaps, F_i in fb[i & 1]: bit v set iff v carries new
+    uint32_t* fb1;          //   sources in round i (pull gathers only from those neighbours)
     RoundCtl* ctl;          // [kMaxRounds]
     uint32_t* t_pre;        // tile lists (compacted per tile): tile-local arc prefix
     int64_t* t_ost;         //   off[u]
@@ -93,13 +97,17 @@ struct Wave {
     const int32_t* pl_big;
     int64_t n_small, n_mid, n_big;
     const int32_t* perm;    // internal vertex -> caller's id for the outputs (nullptr: identity)
+    uint8_t* dist_r;        // [n][P] Delta rows of the wave in internal order, emitted to the
+    uint64_t* masks_r;      // [n][d][P] caller's arrays after the wave; nullptr: the vertex
+                            // phase writes the caller's arrays directly (P = 1, no perm)
+    int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
     int* status;
     float alpha;            // pull threshold factor (<= 0: push only)
 };
 
 // Scratch capacities for n vertices and P slots (entries of each array).
 struct ScratchSizes {
-    int64_t state, queue, list, tiles;
+    int64_t state, queue, list, tiles, bitmap;
 };
 inline ScratchSizes scratch_sizes(int64_t n, int P) {
     ScratchSizes z;
@@ -107,6 +115,7 @@ inline ScratchSizes scratch_sizes(int64_t n, int P) {
     z.queue = n;
     z.list = n + kTileMax;                   // tile slots: ntiles * tile <= n + tile - 1
     z.tiles = (n + kTileMin - 1) / kTileMin + 1;
+    z.bitmap = (n + 31) / 32 + 1;
     return z;
 }
 
@@ -119,6 +128,9 @@ template <int P>
 __global__ void k_phase_a(Wave w, int round);
 template <int P>
 __global__ void k_phase_b(Wave w, int round);
+// Writes the wave's internal rows to the caller's cluster-major outputs.
+template <int P>
+__global__ void k_emit(Wave w, const int32_t* iperm);
 
 // Internal vertex order (cbfs_relabel.cu): ranks by degree, highest first,
 // ties to the smaller id; perm[rank] = id, iperm[id] = rank, off_r = offsets
@@ -131,8 +143,9 @@ cudaError_t relabel_adjacency(int64_t n, int64_t n_big, int64_t n_mid, int64_t n
                               const int32_t* d_iperm, const int64_t* d_off, const int32_t* d_adj, const int64_t* d_off_r,
                               int32_t* d_adj_r, int sms, cudaStream_t st);
 
-// Launches phase A and phase B of one round for w.P (1, 2, 4 or 8).
-cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which /*0 = A, 1 = B*/);
+// Launches phase A (which = 0), phase B (1) of one round, or the emit
+// kernel (2) for w.P (1, 2, 4 or 8).
+cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which, const int32_t* iperm = nullptr);
 
 }  // namespace cbfs
 

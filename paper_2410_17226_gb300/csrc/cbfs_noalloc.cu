@@ -41,7 +41,9 @@ constexpr int64_t kOffAcc = kOffVis + al256(8 * kNoAllocMaxN);
 constexpr int64_t kOffRq = kOffAcc + al256(8 * kNoAllocMaxN);
 constexpr int64_t kOffQ0 = kOffRq + al256(4 * kNoAllocMaxN);
 constexpr int64_t kOffQ1 = kOffQ0 + al256(4 * kNoAllocMaxN);
-constexpr int64_t kOffPre = kOffQ1 + al256(4 * kNoAllocMaxN);
+constexpr int64_t kBitmapWords = (kNoAllocMaxN + 31) / 32 + 1;
+constexpr int64_t kOffFb = kOffQ1 + al256(4 * kNoAllocMaxN);
+constexpr int64_t kOffPre = kOffFb + al256(8 * kBitmapWords);
 constexpr int64_t kOffOst = kOffPre + al256(4 * kListMax);
 constexpr int64_t kOffFw = kOffOst + al256(8 * kListMax);
 constexpr int64_t kOffTileCnt = kOffFw + al256(8 * kListMax);
@@ -119,6 +121,8 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     w.rq = reinterpret_cast<uint32_t*>(base + kOffRq);
     w.q0 = reinterpret_cast<uint32_t*>(base + kOffQ0);
     w.q1 = reinterpret_cast<uint32_t*>(base + kOffQ1);
+    w.fb0 = reinterpret_cast<uint32_t*>(base + kOffFb);
+    w.fb1 = w.fb0 + kBitmapWords;
     w.ctl = reinterpret_cast<RoundCtl*>(base + kOffCtl);
     w.t_pre = reinterpret_cast<uint32_t*>(base + kOffPre);
     w.t_ost = reinterpret_cast<int64_t*>(base + kOffOst);
@@ -131,6 +135,9 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     w.piece_no = reinterpret_cast<uint32_t*>(base + kOffPieceNo);
     w.status = reinterpret_cast<int*>(base + kOffStatus);
     w.alpha = -1.f;  // push only: the dense edge phase needs degree-class lists this variant does not keep
+    w.dist_r = nullptr;  // direct: the vertex phase writes the caller's arrays
+    w.masks_r = nullptr;
+    w.dense_div = 16;
 
     SlotDesc sd;
     memset(&sd, 0, sizeof(sd));
@@ -155,6 +162,7 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     NA_CK(cudaMemsetAsync(w.vis, 0, 8 * (size_t)n, st));
     NA_CK(cudaMemsetAsync(w.acc, 0, 8 * (size_t)n, st));
     NA_CK(cudaMemsetAsync(w.rq, 0, 4 * (size_t)n, st));
+    NA_CK(cudaMemsetAsync(w.fb0, 0, 8 * (size_t)kBitmapWords, st));
     NA_CK(cudaMemsetAsync(w.ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
     NA_CK(cudaMemsetAsync(w.status, 0, sizeof(int), st));
     NA_CK(cudaMemsetAsync(dist, 0xFF, (size_t)n, st));
