@@ -119,18 +119,27 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long x, un
     return s;  // valid in thread 0
 }
 
-// P consecutive words (P * 8 bytes, aligned to min(P * 8, 16)).
+// P consecutive words (P * 8 bytes, aligned to P * 8): one 64-bit access
+// for P = 1, 128-bit for P = 2, 256-bit accesses for P = 4 and 8.
+__device__ __forceinline__ void ld256(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+    asm volatile("ld.global.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+
+__device__ __forceinline__ void st256(uint64_t* p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
+
 template <int P>
 __device__ __forceinline__ void load_words(const uint64_t* p, uint64_t (&x)[P]) {
     if constexpr (P == 1) {
         x[0] = p[0];
+    } else if constexpr (P == 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2*>(p);
+        x[0] = t.x;
+        x[1] = t.y;
     } else {
 #pragma unroll
-        for (int i = 0; i < P; i += 2) {
-            const ulonglong2 t = reinterpret_cast<const ulonglong2*>(p)[i / 2];
-            x[i] = t.x;
-            x[i + 1] = t.y;
-        }
+        for (int i = 0; i < P; i += 4) ld256(p + i, x[i], x[i + 1], x[i + 2], x[i + 3]);
     }
 }
 
@@ -138,9 +147,11 @@ template <int P>
 __device__ __forceinline__ void store_words(uint64_t* p, const uint64_t (&x)[P]) {
     if constexpr (P == 1) {
         p[0] = x[0];
+    } else if constexpr (P == 2) {
+        *reinterpret_cast<ulonglong2*>(p) = make_ulonglong2(x[0], x[1]);
     } else {
 #pragma unroll
-        for (int i = 0; i < P; i += 2) reinterpret_cast<ulonglong2*>(p)[i / 2] = make_ulonglong2(x[i], x[i + 1]);
+        for (int i = 0; i < P; i += 4) st256(p + i, x[i], x[i + 1], x[i + 2], x[i + 3]);
     }
 }
 
@@ -554,19 +565,40 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
     uint64_t all[P];
 #pragma unroll
     for (int s = 0; s < P; ++s) all[s] = sall[s];
-    // CTA per high-degree vertex
-    for (int64_t i = blockIdx.x; i < w.n_big; i += gridDim.x) {
-        const int32_t v = w.pl_big[i];
-        uint64_t vs[P];
-        load_words<P>(w.vis + (size_t)v * P, vs);
-        const unsigned int um = unfinished<P>(vs, all, active);
-        if (!um) continue;  // uniform across the block
+    // high-degree vertices: their lists are cut into kBigDeg-arc pieces that
+    // all CTAs take from a counter; each piece ORs its part into acc[v]
+    for (;;) {
+        if (threadIdx.x == 0) s_work = atomicAdd(&c->piece_ctr, 1u);
+        __syncthreads();
+        const unsigned int p = s_work;
+        __syncthreads();
+        if (p >= w.n_pull_pieces) break;
+        const uint64_t pc = w.pull_pieces[p];
+        const int32_t v = (int32_t)(pc >> 32);
         const int64_t o0 = w.off[v], o1 = w.off[v + 1];
+        const int64_t a0 = o0 + (int64_t)(uint32_t)pc * kBigDeg;
+        const int64_t a1 = min(o1, a0 + kBigDeg);
+        // acc[v] may be growing under other pieces: one thread reads it so that
+        // every thread of the block decides on the same snapshot
+        if (threadIdx.x == 0) {
+            uint64_t vs[P], ac[P];
+            load_words<P>(w.vis + (size_t)v * P, vs);
+            load_words<P>(w.acc + (size_t)v * P, ac);
+#pragma unroll
+            for (int s = 0; s < P; ++s) sor[1][s] = vs[s] | ac[s];
+        }
+        __syncthreads();
+        uint64_t seen[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) seen[s] = sor[1][s];
+        __syncthreads();
+        const unsigned int um = unfinished<P>(seen, all, active);
+        if (!um) continue;  // uniform: seen comes from shared memory
         uint64_t acc[P];
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] = 0;
-        for (int64_t b0 = o0; b0 < o1; b0 += 4 * kThreads) {
-            gather4<P>(w, fb, w.adj, b0 + threadIdx.x, kThreads, o1, acc);
+        for (int64_t b0 = a0; b0 < a1; b0 += 4 * kThreads) {
+            gather4<P>(w, fb, w.adj, b0 + threadIdx.x, kThreads, a1, acc);
 #pragma unroll
             for (int s = 0; s < P; ++s) {
                 const uint64_t wa = warp_or(acc[s]);
@@ -582,9 +614,25 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
 #pragma unroll
             for (int s = 0; s < P; ++s) acc[s] = sor[0][s];
             __syncthreads();
-            if (missing_bits<P>(acc, vs, all, um) == 0) break;
+            if (missing_bits<P>(acc, seen, all, um) == 0) break;
         }
-        if (threadIdx.x == 0) pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
+        if (threadIdx.x == 0) {
+            bool claim = false;
+#pragma unroll
+            for (int s = 0; s < P; ++s) {
+                const uint64_t nb = acc[s] & ~seen[s];
+                if (nb) {
+                    const unsigned long long old =
+                        atomicOr(reinterpret_cast<unsigned long long*>(w.acc + (size_t)v * P + s), (unsigned long long)nb);
+                    claim |= (old == 0ull);
+                }
+            }
+            // the first piece to make acc[v] non-zero counts v once for F_{round+1}
+            if (claim && atomicExch(w.rq + v, stamp) != stamp) {
+                my_cnt += 1;
+                my_sdeg += (unsigned long long)(o1 - o0);
+            }
+        }
     }
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -813,6 +861,7 @@ struct cbfs_graph_s {
     uint64_t* masks_r = nullptr;
     int64_t masks_r_cap = 0;
     int32_t* pl = nullptr;  // pull lists: small | mid | big
+    uint64_t* pull_pieces = nullptr;  // (rank << 32 | piece) of every vertex of degree > kPullMid
     int64_t n_small = 0, n_mid = 0, n_big = 0;
     int64_t big_vertices = 0, big_pieces = 0;
     int grid_p[4] = {0, 0, 0, 0};  // phase-kernel grid for P = 1, 2, 4, 8 (SMs x resident CTAs)
@@ -1115,6 +1164,8 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     w.n_small = g->n_small;
     w.n_mid = g->n_mid;
     w.n_big = g->n_big;
+    w.pull_pieces = g->pull_pieces;
+    w.n_pull_pieces = g->big_pieces;
     w.status = g->status;
     w.alpha = alpha;
     w.dist_r = g->dist_r;
@@ -1304,6 +1355,25 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     } else {
         e = cudaMemsetAsync(g->off_r, 0, sizeof(int64_t), st);
     }
+    // pieces of the high-degree lists for the dense edge phase (ranks [0, n_big))
+    {
+        // piece-major order (every hub's first piece before any second piece):
+        // a later piece usually finds its hub already complete and skips
+        std::vector<uint64_t> pcs;
+        pcs.reserve((size_t)g->big_pieces);
+        for (int64_t k = 0; (int64_t)pcs.size() < g->big_pieces; ++k) {
+            for (int64_t r = 0; r < g->n_big; ++r) {
+                const int64_t dg = off_r[(size_t)r + 1] - off_r[(size_t)r];
+                if (k * kBigDeg < dg) pcs.push_back(((uint64_t)r << 32) | (uint64_t)k);
+                else break;  // ranks are sorted by degree: the rest are shorter
+            }
+        }
+        if (e == cudaSuccess && dev_alloc(&g->pull_pieces, (int64_t)pcs.size()) != CBFS_OK) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess && !pcs.empty())
+            e = cudaMemcpyAsync(g->pull_pieces, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && (int64_t)pcs.size() != g->big_pieces) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // pcs dies with this scope
+    }
     // pull lists in rank space: the degree classes are consecutive rank ranges
     std::vector<int32_t> ranks((size_t)nlist);
     for (int64_t i = 0; i < nlist; ++i) ranks[(size_t)i] = (int32_t)i;
@@ -1338,6 +1408,7 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->adj_r);
     dev_free(g->perm);
     dev_free(g->iperm_d);
+    dev_free(g->pull_pieces);
     dev_free(g->masks_r);
     dev_free(g->pl);
     dev_free(g->ctl);

@@ -92,6 +92,8 @@ struct Wave {
     uint64_t* big_fw;       // [entry][P]
     uint32_t* piece_ent;    // piece p covers arcs [piece_no*kBigDeg, ...) of big[piece_ent]
     uint32_t* piece_no;
+    const uint64_t* pull_pieces;  // pull: (vertex << 32 | piece) for every kBigDeg-arc piece
+    int64_t n_pull_pieces;        //   of every vertex of degree > kPullMid
     const int32_t* pl_small;  // pull lists: vertices by degree class, ascending ids
     const int32_t* pl_mid;
     const int32_t* pl_big;
