@@ -70,6 +70,22 @@ def rank_seed(rank: int) -> int:
     return I.MASTER_SEED + 1 + 1000 * rank
 
 
+def max_over_ranks(x: float, pg, device) -> float:
+    """The slowest rank's time (the job's time): all-reduce MAX; x itself at N = 1."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: int, ranks: int, t_max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time, in G/s."""
+    return units_per_rank * ranks / (t_max_ms / 1e3) / 1e9
+
+
 def workload(scale: int, C: int, rank: int):
     off, adj = I.rmat(scale)
     clusters, d = I.star_clusters(off, adj, C, seed=rank_seed(rank), size="uniform")
@@ -317,17 +333,12 @@ def run_cbfs(args, ws, rank, local):
     prof = g.profile(False)
     t_ms = t_start.elapsed_time(t_end)
     cbfs_ms = sum(a.elapsed_time(b) for a, b in marks)
-    t_max = t_ms
-    if pg:
-        tt = torch.tensor([t_ms], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_ms, pg, dev)
 
     st = g.output_stats(dist, masks, ks, d)
     V, A, R = int(st[:, 0].sum()), int(st[:, 1].sum()), st[:, 2]
     src_edges = int(sum(int(k) * int(r) // 2 for k, r in zip(ks, R)))
-    units = src_edges * args.steps * ws
-    value = units / (t_max / 1e3) / 1e9
+    value = job_value(src_edges * args.steps, ws, t_max)
     alg_bytes_step = ARC_BYTES * A + VERTEX_BYTES * V + C * n * (1 + 8 * d)
     peak, peak_kind = measured_peak_hbm()
     e_launch = prof["edge_phase"]["launches"]

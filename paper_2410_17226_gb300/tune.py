@@ -22,7 +22,7 @@ from . import cbfs
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
 ALPHAS = (0.005, 0.01, 0.02, 0.04, 0.08)
-SLOTS = (1, 2, 4)
+SLOTS = (2, 4, 8)
 
 
 def graph_key(g: "cbfs.Graph", d: int, extra: str = "") -> str:

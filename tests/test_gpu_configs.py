@@ -1,0 +1,177 @@
+"""Parity at the full sizes of the benchmark workloads.
+
+Each test runs the CUDA path in the launch configuration the benchmark uses
+and checks sampled clusters bit for bit against the oracle (Algorithm 1 in C,
+one cluster at a time), plus invariants that hold for every cluster and can
+be checked on the device:
+  * every source S[j] has Delta = 0 and bit j in S[0];
+  * a vertex is unreached exactly when all its stored subsets are empty;
+  * the stored subsets are disjoint and inside ALL.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2410_17226_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def cb():
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2410_17226_gb300 import cbfs
+
+    return cbfs
+
+
+def assert_cluster_equals_oracle(cb, off, adj, S, d, dist_row, masks_rows):
+    od, om = O.cbfs_alg1(off, adj, S, d)
+    gd = dist_row.cpu().numpy()
+    gm = cb.as_numpy_u64(masks_rows)
+    assert (gd == od).all(), f"dist differs at {np.flatnonzero(gd != od)[:5]}"
+    assert (gm == om).all(), "masks differ"
+
+
+def assert_invariants(dist, masks, clusters):
+    """dist uint8 [C, n], masks int64 [C, d, n] on the device."""
+    d = masks.shape[1]
+    for c, S in enumerate(clusters):
+        k = len(S)
+        all_ = -1 if k == 64 else (1 << k) - 1
+        src = torch.as_tensor(np.asarray(S, np.int64), device=dist.device)
+        assert bool((dist[c, src] == 0).all())
+        bits = torch.as_tensor([1 << j if j < 63 else -(1 << 63) for j in range(k)], device=dist.device)
+        if d > 0:
+            assert bool(((masks[c, 0, src] & bits) == bits).all())
+            union = masks[c, 0].clone()
+            for i in range(1, d):
+                assert bool(((union & masks[c, i]) == 0).all())
+                union |= masks[c, i]
+            assert bool(((union & ~torch.tensor(all_, device=dist.device)) == 0).all())
+            assert bool(((dist[c] == 255) == (union == 0)).all())
+
+
+def test_config2_scale22_256_clusters_batched(cb):
+    """Undirected R-MAT scale 22, 256 star clusters of 1..64 sources, d = 2,
+    batched with the autotuned parameters the benchmark uses."""
+    from paper_2410_17226_gb300 import tune
+
+    off, adj = I.rmat(22)
+    clusters, d = I.star_clusters(off, adj, 256, seed=I.MASTER_SEED + 1, size="uniform")
+    g = cb.Graph(off, adj)
+    tn = tune.autotune(g, clusters, d, key_extra=f"rmat-s22-{tune.signature(off)}")
+    tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"]}
+    dist, masks = g.run_batched(clusters, d, tune=tset)
+    assert_invariants(dist, masks, clusters)
+    for c in (0, 131, 255):
+        assert_cluster_equals_oracle(cb, off, adj, clusters[c], d, dist[c], masks[c])
+    for c in (1, 77):
+        sd, sm = g.run(clusters[c], d)
+        assert torch.equal(sd, dist[c]) and torch.equal(sm, masks[c])
+
+
+def test_config3_road_grid_4096_ball_clusters(cb):
+    """4096 x 4096 grid, 10 % of edges deleted, 1 % shortcuts, 64 clusters of
+    64 sources (BFS balls, d = their largest exact diameter), in launches of
+    8 clusters to bound the d-word outputs."""
+    off, adj = I.road_grid(4096)
+    clusters, ds = I.ball_clusters(off, adj, 64, 64, seed=I.MASTER_SEED + 3)
+    d = max(ds)
+    g = cb.Graph(off, adj)
+    checked = 0
+    for b in range(0, 64, 8):
+        part = clusters[b:b + 8]
+        dist, masks = g.run_batched(part, d)
+        assert_invariants(dist, masks, part)
+        if b in (0, 56):
+            assert_cluster_equals_oracle(cb, off, adj, part[0], d, dist[0], masks[0])
+            checked += 1
+        del dist, masks
+    assert checked == 2
+
+
+def test_config4_scale24_1024_degree_clusters_labels(cb):
+    """R-MAT scale 24 (int64 offsets), 1024 degree-ordered clusters of 64
+    (Section 4.2 selection), 32 clusters per launch, labels kept on the device
+    within a 1024 B/vertex budget (60 clusters of 17 B)."""
+    off, adj = I.rmat(24)
+    assert off.dtype == np.int64
+    clusters, d = I.degree_clusters(off, adj, 1024)
+    assert len(clusters) == 1024
+    g = cb.Graph(off, adj)
+    n = g.n
+    budget = 1024 * n
+    cap = budget // (n * (1 + 8 * d)) if n else 0
+    L = cb.Labels(n, int(cap), d, budget_bytes=budget)
+    kept = 0
+    for b in range(0, 1024, 32):
+        part = clusters[b:b + 32]
+        dist, masks = g.run_batched(part, d)
+        if b == 0:
+            assert_cluster_equals_oracle(cb, off, adj, part[0], d, dist[0], masks[0])
+        if b in (0, 992):
+            assert_invariants(dist, masks, part)
+        take = min(len(part), int(cap) - kept)
+        if take > 0:
+            L.append(dist[:take], masks[:take], [len(S) for S in part[:take]])
+            kept += take
+        del dist, masks
+    assert kept == cap == L.count == 60
+    pairs = I.random_pairs(n, 1000, seed=1)
+    ans = cb.as_numpy_u16(L.query(torch.from_numpy(pairs).cuda()))
+    assert L.status() == cb.OK
+    # finite exactly when both ends lie in the landmarks' component, and never
+    # below the true distance (one-sided error, Section 4.2)
+    comp = O.bfs(off, adj, int(clusters[0][0])) >= 0
+    both = comp[pairs[:, 0]] & comp[pairs[:, 1]]
+    assert ((ans != 0xFFFF) == (both | (pairs[:, 0] == pairs[:, 1]))).all()
+    for u, v in pairs[both][:3]:
+        du = O.bfs(off, adj, int(u))
+        a = ans[np.flatnonzero((pairs[:, 0] == u) & (pairs[:, 1] == v))[0]]
+        assert a >= du[v]
+
+
+def test_config5_serving_scale22_labels(cb):
+    """Distance-query serving over the scale-22 graph's device-resident labels
+    (60 degree-ordered clusters): Poisson arrivals of 1..65536-pair requests;
+    results equal alone and in the mix; the query kernel equals the oracle on
+    a two-cluster label store of the same graph."""
+    from paper_2410_17226_gb300.serve import QueryServer, poisson_load
+
+    off, adj = I.rmat(22)
+    clusters, d = I.degree_clusters(off, adj, 60)
+    g = cb.Graph(off, adj)
+    dist, masks = g.run_batched(clusters, d)
+    L = cb.Labels(g.n, 60, d)
+    L.append(dist, masks, [len(S) for S in clusters])
+    with QueryServer(L, max_batch=65536, slots=4) as srv:
+        futs, offered, elapsed = poisson_load(srv, g.n, rate_rps=300.0, duration_s=1.0, max_pairs=65536, seed=7)
+        st = srv.stats()
+    assert st["requests"] == len(futs) and st["pairs"] == offered
+    rng = np.random.default_rng(11)
+    sample = rng.integers(0, g.n, size=(4096, 2)).astype(np.int32)
+    with QueryServer(L, max_batch=65536, slots=2) as srv:
+        alone = srv.submit(sample).result()
+    mixed_srv = QueryServer(L, max_batch=8192, slots=4)
+    noise = [mixed_srv.submit(rng.integers(0, g.n, size=(int(rng.integers(1, 20000)), 2)).astype(np.int32))
+             for _ in range(8)]
+    mixed = mixed_srv.submit(sample)
+    for f in noise:
+        f.result()
+    mixed = mixed.result()
+    mixed_srv.close()
+    assert (alone == mixed).all()
+    # the query itself against the oracle on two of the clusters
+    two = [clusters[0], clusters[59]]
+    od = np.zeros((2, g.n), np.uint8)
+    om = np.zeros((2, d, g.n), np.uint64)
+    for i, S in enumerate(two):
+        od[i], om[i] = O.cbfs_alg1(off, adj, S, d)
+    L2 = cb.Labels(g.n, 2, d)
+    L2.append(torch.from_numpy(od).cuda(), torch.from_numpy(om.view(np.int64)).cuda(), [len(S) for S in two])
+    got = cb.as_numpy_u16(L2.query(torch.from_numpy(sample).cuda()))
+    assert (got == O.query(od, om, [len(S) for S in two], sample)).all()

@@ -1,0 +1,95 @@
+"""Serving: continuous batching of distance queries over device-resident
+labels.  Each request's answers must be identical whether it is served alone
+or mixed with many concurrent requests of other sizes, and equal to the
+oracle's landmark query."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2410_17226_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2410_17226_gb300 import cbfs
+
+    off, adj = I.rmat(12, seed=17)
+    clusters, d = I.degree_clusters(off, adj, 12)
+    g = cbfs.Graph(off, adj)
+    dist, masks = g.run_batched(clusters, d)
+    L = cbfs.Labels(g.n, len(clusters), d)
+    ks = [len(S) for S in clusters]
+    L.append(dist, masks, ks)
+    torch.cuda.synchronize()
+    return cbfs, g, L, dist.cpu().numpy(), cbfs.as_numpy_u64(masks), ks
+
+
+def make_requests(n, count, seed, max_pairs):
+    rng = np.random.default_rng(seed)
+    return [rng.integers(0, n, size=(int(rng.integers(1, max_pairs + 1)), 2)).astype(np.int32) for _ in range(count)]
+
+
+def test_alone_equals_in_the_mix_and_oracle(setup):
+    cbfs, g, L, dist, masks, ks = setup
+    from paper_2410_17226_gb300.serve import QueryServer
+
+    reqs = make_requests(g.n, 60, seed=1, max_pairs=3000)
+    reqs.append(np.zeros((0, 2), np.int32))
+    alone = []
+    with QueryServer(L, max_batch=1024, slots=2) as srv:
+        for r in reqs:
+            alone.append(srv.submit(r).result())  # one request in flight at a time
+    mixed = [None] * len(reqs)
+    with QueryServer(L, max_batch=1024, slots=4, memory_budget_bytes=3 * 1024 * 10) as srv:
+        futs = {}
+
+        def client(lo, hi):
+            for i in range(lo, hi):
+                futs[i] = srv.submit(reqs[i])
+
+        ts = [threading.Thread(target=client, args=(i, min(i + 16, len(reqs)))) for i in range(0, len(reqs), 16)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        for i, f in futs.items():
+            mixed[i] = f.result()
+        st = srv.stats()
+    assert st["requests"] == len(reqs) - 1 or st["requests"] == len(reqs)
+    assert st["batches"] >= 2
+    for r, a, m in zip(reqs, alone, mixed):
+        assert a.dtype == np.uint16 and a.shape == (r.shape[0],)
+        assert (a == m).all()
+        if r.shape[0]:
+            assert (a == O.query(dist, masks, ks, r)).all()
+
+
+def test_large_request_split_over_batches(setup):
+    cbfs, g, L, dist, masks, ks = setup
+    from paper_2410_17226_gb300.serve import QueryServer
+
+    big = np.random.default_rng(3).integers(0, g.n, size=(5000, 2)).astype(np.int32)
+    with QueryServer(L, max_batch=512, slots=2) as srv:
+        got = srv.submit(big).result()
+        assert srv.stats()["batches"] >= 10
+    assert (got == O.query(dist, masks, ks, big)).all()
+
+
+def test_poisson_load_reports_latency(setup):
+    cbfs, g, L, dist, masks, ks = setup
+    from paper_2410_17226_gb300.serve import QueryServer, poisson_load
+
+    with QueryServer(L, max_batch=4096, slots=3) as srv:
+        futs, offered, elapsed = poisson_load(srv, g.n, rate_rps=400.0, duration_s=0.5, max_pairs=2000, seed=5)
+        st = srv.stats()
+    assert st["requests"] == len(futs)
+    assert st["pairs"] == offered
+    assert st["p99_ms"] >= st["p50_ms"] >= 0
