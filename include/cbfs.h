@@ -72,7 +72,12 @@ typedef struct cbfs_tune_s {
     /* the vertex phase scans every vertex instead of the frontier queue when
        |F| * dense_div > n.  0 = default (16); < 0 = never. */
     int dense_div;
-    int reserved[5];
+    /* != 0: drive the rounds from the host (one launch per kernel, a
+       synchronisation every two rounds) instead of one CUDA graph per call
+       whose rounds loop on the device (conditional WHILE nodes).  Calls with
+       kernel timing enabled (cbfs_profile) always use the host loop. */
+    int host_loop;
+    int reserved[4];
 } cbfs_tune_t;
 
 /* Work counters of one cluster's traversal (Theorem 1). */

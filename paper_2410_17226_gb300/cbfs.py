@@ -37,7 +37,7 @@ class CbfsError(RuntimeError):
 
 class Tune(ctypes.Structure):
     _fields_ = [("pull_alpha", ctypes.c_float), ("slots", ctypes.c_int), ("dense_div", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("host_loop", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class KernelTimes(ctypes.Structure):
@@ -220,6 +220,7 @@ class Graph:
             t.pull_alpha = float(tune.get("pull_alpha", 0.0))
             t.slots = int(tune.get("slots", 0))
             t.dense_div = int(tune.get("dense_div", 0))
+            t.host_loop = int(tune.get("host_loop", 0))
         src_p = src.ctypes.data if src.size else np.zeros(1, np.int32).ctypes.data
         rc = lib().cbfs_run_batched(self._h, src_p, coff.ctypes.data, int(C), int(d), _ptr(dist),
                                     _ptr(masks) if d > 0 else None, ctypes.byref(t), _stream_ptr(stream))

@@ -47,6 +47,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "cbfs_internal.cuh"
@@ -321,6 +322,24 @@ __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count) {
     }
 }
 
+// Graph mode: after phase B of the current round, continue the round loop
+// while the next frontier is not empty (and the round bound allows it).
+__global__ void k_round_cond(Wave w, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    const int r = *w.round_dev;
+    unsigned int go = 0;
+    atomicAdd(w.iters, 1ull);
+    if (w.ctl[r + 1].qlen > 0) {
+        if (r + 2 < kMaxRounds) {
+            *w.round_dev = r + 1;
+            go = 1;
+        } else {
+            set_status(w.status, CBFS_E_DEPTH);
+        }
+    }
+    cudaGraphSetConditional(h, go);
+}
+
 // Phase A: the vertex phase of round `round`, the direction decision and,
 // for a push round, the push work lists.  A small frontier is read from the
 // queue; a large one (qlen * dense_div > n) by scanning every vertex in
@@ -334,6 +353,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     __shared__ ScanSmem scan;
     __shared__ unsigned long long red[kWarps];
     __shared__ unsigned int s_active;
+    if (w.round_dev) round = *w.round_dev;
     RoundCtl* c = w.ctl + round;
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
@@ -484,6 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
     __shared__ unsigned int s_work;
     __shared__ uint64_t sor[kWarps][P];
     __shared__ int32_t sadj[kWarps][32 * kPullSmall];
+    if (w.round_dev) round = *w.round_dev;
     RoundCtl* c = w.ctl + round;
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
@@ -904,6 +925,17 @@ struct cbfs_graph_s {
     uint64_t launches[3] = {0, 0, 0};
     double ms[3] = {0, 0, 0};
     uint64_t total_launches = 0;
+    // graph mode: device round counter, capture streams, instantiated graphs
+    int* round_dev = nullptr;
+    unsigned long long* iters = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;
+    struct GraphEntry {
+        uint64_t key;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;  // most recently used last
+    std::vector<uint64_t> seen;      // call shapes run once (host-driven) and not yet captured
 };
 
 namespace {
@@ -1070,6 +1102,93 @@ int check_clusters(const cbfs_graph_s* g, const int32_t* src, const int32_t* cof
     return CBFS_OK;
 }
 
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Records every wave of a call as one CUDA graph: per wave the state
+// memsets, the seed kernel, a conditional WHILE node whose body is phase A,
+// phase B and k_round_cond, then the emit and the source check.
+int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vector<int64_t>& seed_off, int grid,
+                int64_t bm_words, cudaGraphExec_t* out) {
+    *out = nullptr;
+    if (!g->cap_stream) {
+        CK(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&g->cap_stream2, cudaStreamNonBlocking));
+    }
+    cudaStream_t cs = g->cap_stream, cs2 = g->cap_stream2;
+    const int64_t n = g->n;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (size_t wv = 0; wv < waves.size() && e == cudaSuccess; ++wv) {
+        const Wave& w = waves[wv];
+        const int P = w.P, d = w.d;
+        const int cnt = (int)(seed_off[wv + 1] - seed_off[wv]);
+        e = cudaMemsetAsync(w.vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.rq, 0, sizeof(uint32_t) * (size_t)n, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.fb0, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.dist_r, 0xFF, (size_t)P * (size_t)n, cs);
+        if (e == cudaSuccess && d) e = cudaMemsetAsync(w.masks_r, 0, sizeof(uint64_t) * (size_t)P * d * n, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, sizeof(RoundCtl) * kMaxRounds, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.round_dev, 0, sizeof(int), cs);
+        if (e != cudaSuccess) break;
+        k_seed<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        // the round loop: a conditional WHILE node spliced into the capture
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps)) != cudaSuccess) break;
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        if ((e = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, &cp)) != cudaSuccess) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            break;
+        if ((e = cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            break;
+        cudaError_t eb = launch_round(w, 0, grid, cs2, 0);
+        if (eb == cudaSuccess) eb = launch_round(w, 0, grid, cs2, 1);
+        if (eb == cudaSuccess) {
+            k_round_cond<<<1, 32, 0, cs2>>>(w, h);
+            eb = cudaGetLastError();
+        }
+        cudaGraph_t body_out = nullptr;
+        e = cudaStreamEndCapture(cs2, &body_out);
+        if (e == cudaSuccess) e = eb;
+        if (e != cudaSuccess) break;
+        if ((e = launch_round(w, 0, grid, cs, 2, g->iperm_d)) != cudaSuccess) break;
+        k_check_sources<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt);
+        e = cudaGetLastError();
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g_last_cuda_error = e;
+        cudaGetLastError();
+        *out = nullptr;
+        return CBFS_E_CUDA;
+    }
+    return CBFS_OK;
+}
+
 // Clusters per wave: the requested slot count rounded down to a power of
 // two (1, 2, 4, 8), no wider than the number of clusters.
 int slots_for(const cbfs_tune_t* tune, int C) {
@@ -1171,6 +1290,70 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     w.dist_r = g->dist_r;
     w.masks_r = g->masks_r;
     w.dense_div = dense_div;
+
+    // Graph mode: a call shape seen before runs as one cached CUDA graph whose
+    // rounds loop on the device; a first sighting runs host-driven below and
+    // is remembered, so one-off calls (a fresh handle) pay no capture.
+    if (!g->timing && !(tune && tune->host_loop)) {
+        if (!g->round_dev) {
+            rc = dev_alloc(&g->round_dev, 1);
+            if (!rc) rc = dev_alloc(&g->iters, 1);
+            if (rc) return rc;
+        }
+        Wave wg = w;
+        wg.round_dev = g->round_dev;
+        wg.iters = g->iters;
+        std::vector<Wave> waves((size_t)nwaves, wg);
+        uint64_t key = 1469598103934665603ull;
+        for (int wv = 0; wv < nwaves; ++wv) {
+            waves[wv].nslots = std::min(P, C - wv * P);
+            waves[wv].slots = g->slots + (size_t)wv * P;
+            key = fnv1a(key, &waves[wv], sizeof(Wave));
+        }
+        key = fnv1a(key, wave_seed_off.data(), sizeof(int64_t) * wave_seed_off.size());
+        key = fnv1a(key, &grid, sizeof(grid));
+        cudaGraphExec_t exec = nullptr;
+        for (size_t i = 0; i < g->graphs.size(); ++i) {
+            if (g->graphs[i].key == key) {
+                const auto ge = g->graphs[i];
+                g->graphs.erase(g->graphs.begin() + (long)i);
+                g->graphs.push_back(ge);
+                exec = ge.exec;
+                break;
+            }
+        }
+        if (!exec) {
+            bool repeat = false;
+            for (uint64_t k : g->seen) repeat |= (k == key);
+            if (repeat) {
+                rc = build_graph(g, waves, wave_seed_off, grid, bm_words, &exec);
+                if (rc) return rc;
+                if (g->graphs.size() >= 8) {
+                    cudaGraphExecDestroy(g->graphs.front().exec);
+                    g->graphs.erase(g->graphs.begin());
+                }
+                g->graphs.push_back({key, exec});
+            } else {
+                if (g->seen.size() >= 16) g->seen.erase(g->seen.begin());
+                g->seen.push_back(key);
+            }
+        }
+        if (exec) {
+            CK(cudaMemsetAsync(g->iters, 0, sizeof(unsigned long long), st));
+            CK(cudaGraphLaunch(exec, st));
+            int status = 0;
+            unsigned long long iters = 0;
+            CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(&iters, g->iters, sizeof(iters), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            // per wave: seed, emit, check; per round: phase A, phase B, condition
+            g->launches[0] += 3ull * (uint64_t)nwaves;
+            g->launches[1] += iters;
+            g->launches[2] += iters;
+            g->total_launches += 3ull * (uint64_t)nwaves + 3ull * iters;
+            return status;
+        }
+    }
 
     for (int wv = 0; wv < nwaves; ++wv) {
         const int c0 = wv * P;
@@ -1416,6 +1599,11 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->slots);
     dev_free(g->seeds);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
+    for (auto& ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->cap_stream2) cudaStreamDestroy(g->cap_stream2);
+    dev_free(g->round_dev);
+    dev_free(g->iters);
     if (g->h_q) cudaFreeHost(g->h_q);
     if (g->h_slots) cudaFreeHost(g->h_slots);
     if (g->h_seeds) cudaFreeHost(g->h_seeds);

@@ -103,6 +103,8 @@ struct Wave {
     uint64_t* masks_r;      // [n][d][P] caller's arrays after the wave; nullptr: the vertex
                             // phase writes the caller's arrays directly (P = 1, no perm)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
+    int* round_dev;         // graph mode: the current round lives here (nullptr: kernel argument)
+    unsigned long long* iters;  // graph mode: rounds executed (for the launch accounting)
     int* status;
     float alpha;            // pull threshold factor (<= 0: push only)
 };

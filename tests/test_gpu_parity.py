@@ -97,15 +97,35 @@ def test_batched_equals_single_and_oracle(cb):
     clusters, d = I.star_clusters(off, adj, 19, seed=4, size="uniform")
     single = [g.run(S, d) for S in clusters]
     for tune in (None, {"slots": 1}, {"slots": 3}, {"slots": 16}, dict(PUSH_ONLY, slots=4),
-                 dict(PULL_EAGER, slots=5)):
-        bd, bm = g.run_batched(clusters, d, tune=tune)
-        for c, (sd, sm) in enumerate(single):
-            assert torch.equal(bd[c], sd), (tune, c)
-            assert torch.equal(bm[c], sm), (tune, c)
+                 dict(PULL_EAGER, slots=5), {"slots": 8, "host_loop": 1}, {"slots": 2, "dense_div": -1},
+                 {"slots": 4, "dense_div": 1}, dict(PUSH_ONLY, slots=8, host_loop=1)):
+        # the first call of a shape runs host-driven, a repeat replays a CUDA graph
+        for rep in range(2):
+            bd, bm = g.run_batched(clusters, d, tune=tune)
+            for c, (sd, sm) in enumerate(single):
+                assert torch.equal(bd[c], sd), (tune, rep, c)
+                assert torch.equal(bm[c], sm), (tune, rep, c)
     for c, S in enumerate(clusters):
         od, om = O.cbfs_alg1(off, adj, S, d)
         assert (single[c][0].cpu().numpy() == od).all()
         assert (cb.as_numpy_u64(single[c][1]) == om).all()
+
+
+def test_graph_replay_with_new_sources_each_call(cb):
+    """A cached graph replays a call shape; the sources of every call are
+    uploaded before the replay, so different clusters of the same shape give
+    their own results."""
+    off, adj = I.rmat(12, seed=5)
+    g = cb.Graph(off, adj)
+    for seed in range(4):
+        clusters, d = I.star_clusters(off, adj, 6, seed=100 + seed, size="max")
+        clusters = [c[:5] if len(c) >= 5 else c for c in clusters]
+        if any(len(c) != 5 for c in clusters):
+            continue
+        bd, bm = g.run_batched(clusters, d, tune={"slots": 2})
+        for c, S in enumerate(clusters):
+            od, om = O.cbfs_alg1(off, adj, S, d)
+            assert (bd[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(bm[c]) == om).all(), (seed, c)
 
 
 def test_hubs_and_big_lists(cb):
