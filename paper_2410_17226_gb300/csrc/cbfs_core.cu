@@ -495,15 +495,20 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
 
 // Phase B: the edge phase of round `round` in the direction phase A chose.
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_phase_b(Wave w, int round) {
+__global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, int round) {
     constexpr int TILE = Geo<P>::kTile;
-    __shared__ uint32_t spre[kThreads + 1];
-    __shared__ int64_t sost[kThreads];
-    __shared__ uint64_t sfw[kThreads * P];
+    // push and pull never run in the same launch: their staging buffers overlap
+    constexpr int kPushPre = (4 * (kThreads + 1) + 15) / 16 * 16;
+    constexpr int kPushBytes = kPushPre + 8 * kThreads + 8 * kThreads * P;
+    constexpr int kPullBytes = 4 * kWarps * 32 * (int)kPullSmall;
+    __shared__ __align__(16) unsigned char sraw[kPushBytes > kPullBytes ? kPushBytes : kPullBytes];
+    uint32_t* spre = reinterpret_cast<uint32_t*>(sraw);                      // push: [kThreads + 1]
+    int64_t* sost = reinterpret_cast<int64_t*>(sraw + kPushPre);             // push: [kThreads]
+    uint64_t* sfw = reinterpret_cast<uint64_t*>(sraw + kPushPre + 8 * kThreads);  // push: [kThreads * P]
+    int32_t(*sadj)[32 * kPullSmall] = reinterpret_cast<int32_t(*)[32 * kPullSmall]>(sraw);  // pull
     __shared__ uint64_t sall[P];
     __shared__ unsigned int s_work;
     __shared__ uint64_t sor[kWarps][P];
-    __shared__ int32_t sadj[kWarps][32 * kPullSmall];
     if (w.round_dev) round = *w.round_dev;
     RoundCtl* c = w.ctl + round;
     const unsigned long long qlen = c->qlen;
