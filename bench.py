@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-requests", type=int, default=200)
+    ap.add_argument("--serve-s", type=float, default=2.0, help="seconds per offered serving load (0: skip)")
     ap.add_argument("--fixed-tune", default="", help="'alpha,slots' instead of the autotuner (profiling runs)")
     return ap.parse_args()
 
@@ -382,6 +383,43 @@ def run_cbfs(args, ws, rank, local):
              "qps": round(qtot / q_wall, 1), "requests": len(lat), "clusters": C,
              "mode": "one request at a time, sizes U{1..65536}, pinned H2D + kernel + D2H"}
 
+    # serving (continuous batching) over labels of 60 degree-ordered clusters of the same graph
+    serving = None
+    if args.serve_s > 0:
+        from paper_2410_17226_gb300.serve import QueryServer, poisson_load
+
+        lab_clusters, _ = I.degree_clusters(off, adj, 60)
+        ld, lm = g.run_batched(lab_clusters, d, tune=tset)
+        L60 = cbfs.Labels(n, len(lab_clusters), d)
+        L60.append(ld, lm, [len(S) for S in lab_clusters])
+        del ld, lm
+        torch.cuda.synchronize()
+        with QueryServer(L60, max_batch=args.query_batch, slots=4) as srv:
+            rng = np.random.default_rng(rank_seed(rank) + 13)
+            big = rng.integers(0, n, size=(args.query_batch, 2)).astype(np.int32)
+            for _ in range(4):
+                srv.submit(big).result()  # warm
+            t0 = time.perf_counter()
+            futs = [srv.submit(big) for _ in range(64)]
+            for f in futs:
+                f.result()
+            sat_qps = 64 * args.query_batch / (time.perf_counter() - t0)
+        loads = {}
+        mean_req = (args.query_batch + 1) / 2.0
+        for load in (0.5, 0.8):
+            with QueryServer(L60, max_batch=args.query_batch, slots=4) as srv:
+                futs, offered, elapsed = poisson_load(srv, n, rate_rps=load * sat_qps / mean_req,
+                                                      duration_s=args.serve_s, max_pairs=args.query_batch,
+                                                      seed=rank_seed(rank) + int(load * 100))
+                st_ = srv.stats()
+            loads[f"{load}x"] = {"p50_ms": round(st_["p50_ms"], 4), "p99_ms": round(st_["p99_ms"], 4),
+                                 "qps": round(offered / elapsed, 1), "requests": st_["requests"],
+                                 "batches": st_["batches"]}
+        serving = {"labels": "60 degree-ordered clusters (Section 4.2 selection), d=2, 1020 B/vertex",
+                   "arrivals": "Poisson, request sizes uniform in 1..65536 pairs", "saturation_qps": round(sat_qps, 1),
+                   "offered": loads}
+        del L60
+
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -436,6 +474,7 @@ def run_cbfs(args, ws, rank, local):
             "work_per_step": {"V": V, "A": A, "source_edges": src_edges, "alg_bytes": int(alg_bytes_step)},
             "kernel_ms_one_untimed_step": {k: split[k] for k in ("setup", "vertex_phase", "edge_phase")},
             "query": query,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if pg:

@@ -207,23 +207,30 @@ class QueryServer:
 
 def poisson_load(server: QueryServer, n: int, rate_rps: float, duration_s: float, max_pairs: int, seed: int):
     """Offers requests with exponential inter-arrival times (rate_rps per
-    second) and sizes uniform in 1..max_pairs for duration_s seconds.
-    Returns (futures, pairs offered, elapsed seconds)."""
+    second) and sizes uniform in 1..max_pairs for duration_s seconds; each
+    request is a slice of a pregenerated pool of uniform random pairs, so the
+    client itself is not the bottleneck.  Returns (futures, pairs offered,
+    elapsed seconds)."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    pool = rng.integers(0, n, size=(4 * max_pairs, 2), dtype=np.int64).astype(np.int32)
+    gaps = rng.exponential(1.0 / rate_rps, size=1 << 16)
+    sizes = rng.integers(1, max_pairs + 1, size=1 << 16)
+    starts = rng.integers(0, 3 * max_pairs + 1, size=1 << 16)
     futs, offered = [], 0
     t0 = time.perf_counter()
     t_next = t0
+    i = 0
     while True:
-        t_next += rng.exponential(1.0 / rate_rps)
+        t_next += gaps[i % gaps.size]
         if t_next - t0 > duration_s:
             break
         now = time.perf_counter()
         if t_next > now:
             time.sleep(t_next - now)
-        q = int(rng.integers(1, max_pairs + 1))
-        pairs = rng.integers(0, n, size=(q, 2), dtype=np.int64).astype(np.int32)
-        futs.append(server.submit(pairs))
+        q, s0 = int(sizes[i % sizes.size]), int(starts[i % starts.size])
+        futs.append(server.submit(pool[s0:s0 + q]))
         offered += q
+        i += 1
     for f in futs:
         f.result()
     return futs, offered, time.perf_counter() - t0
