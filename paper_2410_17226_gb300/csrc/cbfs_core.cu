@@ -1500,7 +1500,12 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     sms = std::max(1, sms);
     const void* kb[4] = {(const void*)k_phase_b<1>, (const void*)k_phase_b<2>, (const void*)k_phase_b<4>,
                          (const void*)k_phase_b<8>};
+    const void* ka[4] = {(const void*)k_phase_a<1>, (const void*)k_phase_a<2>, (const void*)k_phase_a<4>,
+                         (const void*)k_phase_a<8>};
     for (int i = 0; i < 4; ++i) {
+        // the largest shared-memory carveout, so that shared memory never caps the resident CTAs
+        cudaFuncSetAttribute(kb[i], cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(ka[i], cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
         occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb[i], kThreads, 0);
         g->grid_p[i] = sms * std::max(1, std::min(occ, 8));
