@@ -194,7 +194,8 @@ __device__ __forceinline__ void gather4(const Wave& w, const uint32_t* fb, const
 
 // Appends v to the next frontier and adds deg to its degree sum (the
 // direction decision of the next round); one atomic pair per warp.
-__device__ __forceinline__ void append_next(uint32_t* q, RoundCtl* cn, uint32_t v, uint32_t deg) {
+__device__ __forceinline__ void append_next(uint32_t* q, RoundCtl* cn, uint32_t* fbn, uint32_t v, uint32_t deg) {
+    atomicOr(fbn + (v >> 5), 1u << (v & 31));
     const unsigned mask = __activemask();
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(mask) - 1;
@@ -213,7 +214,7 @@ __device__ __forceinline__ void append_next(uint32_t* q, RoundCtl* cn, uint32_t 
 // Push the new sources fw[0..P) of a frontier vertex along one arc to t.
 template <int P>
 __device__ __forceinline__ void push_arc(const Wave& w, const uint64_t* fw, uint32_t t, uint32_t stamp, uint32_t* qn,
-                                         RoundCtl* cn) {
+                                         RoundCtl* cn, uint32_t* fbn) {
     uint64_t vs[P], b[P];
     load_words<P>(w.vis + (size_t)t * P, vs);  // vis is read-only in phase B
     uint64_t any = 0;
@@ -237,7 +238,7 @@ __device__ __forceinline__ void push_arc(const Wave& w, const uint64_t* fw, uint
     }
     if (!claim) return;
     if (P == 1 || atomicExch(w.rq + t, stamp) != stamp)
-        append_next(qn, cn, t, (uint32_t)(w.off[t + 1] - w.off[t]));
+        append_next(qn, cn, fbn, t, (uint32_t)(w.off[t + 1] - w.off[t]));
 }
 
 // Direction of a round (Algorithm "EdgeMap"): dense when the frontier and
@@ -272,7 +273,7 @@ __device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], cons
 // queue (the next vertex phase scans densely); it only counts the new
 // frontier and its arcs for the next direction decision.
 template <int P>
-__device__ __forceinline__ void pull_finish(const Wave& w, int32_t v, const uint64_t (&acc)[P], const uint64_t (&vs)[P],
+__device__ __forceinline__ bool pull_finish(const Wave& w, int32_t v, const uint64_t (&acc)[P], const uint64_t (&vs)[P],
                                             uint32_t deg, unsigned long long& cnt, unsigned long long& sdeg) {
     uint64_t nw[P], any = 0;
 #pragma unroll
@@ -285,6 +286,7 @@ __device__ __forceinline__ void pull_finish(const Wave& w, int32_t v, const uint
         cnt += 1;
         sdeg += deg;
     }
+    return any != 0;
 }
 
 }  // namespace
@@ -306,6 +308,7 @@ __global__ void k_seed(Wave w, const uint64_t* seeds, int count) {
         if (atomicExch(w.rq + v, 1u) != 1u) {
             append(w.q0, &w.ctl[0].qlen, v);
             atomicAdd(&w.ctl[0].sdeg, (unsigned long long)(w.off[v + 1] - w.off[v]));
+            atomicOr(w.fb0 + (v >> 5), 1u << (v & 31));
         }
     }
 }
@@ -364,7 +367,14 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
     const uint32_t* q = (round & 1) ? w.q1 : w.q0;
-    uint32_t* fbw = (round & 1) ? w.fb1 : w.fb0;
+    const uint32_t* fbr = (round & 1) ? w.fb1 : w.fb0;  // F_round, set by its producers
+    {
+        // F_{round+1}'s bitmap was last read in round - 1: clear it for this round's edge phase
+        uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
+        const int64_t words = (w.n + 31) / 32;
+        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads)
+            fbn[i] = 0u;
+    }
     const unsigned long long span = dense ? (unsigned long long)w.n : qlen;
     const unsigned long long ntiles = (span + TILE - 1) / TILE;
     unsigned long long my_nf = 0;
@@ -383,6 +393,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             for (int s = 0; s < P; ++s) fw[r][s] = 0;
             const unsigned long long idx = t * TILE + (unsigned long long)threadIdx.x * EPT + r;
             if (idx >= span) continue;
+            if (dense && !((fbr[idx >> 5] >> (idx & 31)) & 1u)) continue;  // not in F_round
             const uint32_t u = dense ? (uint32_t)idx : q[idx];
             uint64_t a[P], vs[P];
             load_words<P>(w.acc + (size_t)u * P, a);
@@ -401,7 +412,6 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             store_words<P>(w.vis + (size_t)u * P, vs);
             zero_words<P>(w.acc + (size_t)u * P);
             if (!any) continue;
-            atomicOr(fbw + (u >> 5), 1u << (u & 31));
             if (w.dist_r) {
                 // the wave's internal rows of u
                 uint8_t* dr = w.dist_r + (size_t)u * P;
@@ -519,14 +529,10 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     RoundCtl* cn = w.ctl + round + 1;
     const uint32_t stamp = (uint32_t)round + 2;  // F_{round+1}
     const bool pull = c->mode != 0;
-    {
-        // F_{round+1}'s bitmap was last read in round - 1: clear it for phase A of round + 1
-        uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
-        const int64_t words = (w.n + 31) / 32;
-        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads)
-            fbn[i] = 0u;
-    }
+    // F_round's bitmap (read) and F_{round+1}'s (written by whoever adds a vertex;
+    // phase A of this round cleared it)
     const uint32_t* fb = (round & 1) ? w.fb1 : w.fb0;
+    uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
 
     if (!pull) {
         // big-list pieces: kBigDeg consecutive arcs of one hub per CTA step
@@ -542,7 +548,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
             const int64_t a0 = (int64_t)w.piece_no[p] * kBigDeg;
             const int64_t a1 = min(be.deg, a0 + kBigDeg);
             for (int64_t a = a0 + threadIdx.x; a < a1; a += kThreads)
-                push_arc<P>(w, sfw, (uint32_t)w.adj[be.ost + a], stamp, qn, cn);
+                push_arc<P>(w, sfw, (uint32_t)w.adj[be.ost + a], stamp, qn, cn, fbn);
             __syncthreads();
         }
         // tiles: entries of degree <= kBigDeg, arcs spread over the threads
@@ -577,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
                         if (spre[mid] <= a) lo = mid;
                         else hi = mid - 1;
                     }
-                    push_arc<P>(w, sfw + lo * P, (uint32_t)w.adj[sost[lo] + (a - spre[lo])], stamp, qn, cn);
+                    push_arc<P>(w, sfw + lo * P, (uint32_t)w.adj[sost[lo] + (a - spre[lo])], stamp, qn, cn, fbn);
                 }
                 __syncthreads();
             }
@@ -657,6 +663,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
             if (claim && atomicExch(w.rq + v, stamp) != stamp) {
                 my_cnt += 1;
                 my_sdeg += (unsigned long long)(o1 - o0);
+                atomicOr(fbn + (v >> 5), 1u << (v & 31));
             }
         }
     }
@@ -681,7 +688,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
             for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
             if (missing_bits<P>(acc, vs, all, um) == 0) break;
         }
-        if (lane == 0) pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
+        if (lane == 0 && pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg))
+            atomicOr(fbn + (v >> 5), 1u << (v & 31));
     }
     // low-degree vertices: a warp takes 32 consecutive ones, whose lists are
     // consecutive in the internal order, stages them in shared memory with
@@ -697,6 +705,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         const int64_t hi = __shfl_sync(0xffffffffu, o1, last);
         for (int64_t x = lo + lane; x < hi; x += 32) wadj[x - lo] = w.adj[x];
         __syncwarp();
+        bool joined = false;
         if (has) {
             uint64_t vs[P];
             load_words<P>(w.vis + (size_t)v * P, vs);
@@ -709,8 +718,16 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
                     gather4<P>(w, fb, wadj - lo, e, 1, o1, acc);
                     if (missing_bits<P>(acc, vs, all, um) == 0) break;
                 }
-                pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
+                joined = pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
             }
+        }
+        // the 32 vertices are consecutive: their bits span at most two bitmap words
+        const unsigned int jm = __ballot_sync(0xffffffffu, joined);
+        if (lane == 0 && jm) {
+            const int32_t v0 = w.pl_small[g0];
+            const int sh = v0 & 31;
+            atomicOr(fbn + (v0 >> 5), jm << sh);
+            if (sh && (jm >> (32 - sh))) atomicOr(fbn + (v0 >> 5) + 1, jm >> (32 - sh));
         }
         __syncwarp();
     }
@@ -1500,12 +1517,9 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     sms = std::max(1, sms);
     const void* kb[4] = {(const void*)k_phase_b<1>, (const void*)k_phase_b<2>, (const void*)k_phase_b<4>,
                          (const void*)k_phase_b<8>};
-    const void* ka[4] = {(const void*)k_phase_a<1>, (const void*)k_phase_a<2>, (const void*)k_phase_a<4>,
-                         (const void*)k_phase_a<8>};
     for (int i = 0; i < 4; ++i) {
-        // the largest shared-memory carveout, so that shared memory never caps the resident CTAs
-        cudaFuncSetAttribute(kb[i], cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(ka[i], cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+        // the default carveout: a larger shared-memory share would shrink the L1 these
+        // gather-bound kernels depend on (measured slower)
         occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb[i], kThreads, 0);
         g->grid_p[i] = sms * std::max(1, std::min(occ, 8));
