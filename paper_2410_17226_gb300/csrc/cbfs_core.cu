@@ -164,22 +164,30 @@ __device__ __forceinline__ void zero_words(uint64_t* p) {
     store_words<P>(p, z);
 }
 
-// ORs into acc the vis blocks of the frontier neighbours among up to four
-// arcs adj[e], adj[e + step], ... below o1; all gathers are issued before any
-// is used.
+// Gathers kept in flight per lane (two for P = 8 measured slower: the
+// register saving did not pay for the lost memory-level parallelism).
 template <int P>
-__device__ __forceinline__ void gather4(const Wave& w, const uint32_t* fb, const int32_t* adj, int64_t e, int64_t step,
-                                        int64_t o1, uint64_t (&acc)[P]) {
-    int32_t u[4];
+struct Gath {
+    static constexpr int G = 4;
+};
+
+// ORs into acc the vis blocks of the frontier neighbours among up to G arcs
+// adj[e], adj[e + step], ... below o1 (fb == nullptr: every neighbour); all
+// gathers are issued before any is used.
+template <int P>
+__device__ __forceinline__ void gather(const Wave& w, const uint32_t* fb, const int32_t* adj, int64_t e, int64_t step,
+                                       int64_t o1, uint64_t (&acc)[P]) {
+    constexpr int G = Gath<P>::G;
+    int32_t u[G];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) u[k] = (e + k * step < o1) ? adj[e + k * step] : -1;
+    for (int k = 0; k < G; ++k) u[k] = (e + k * step < o1) ? adj[e + k * step] : -1;
     // only frontier neighbours can carry sources v has not seen
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (u[k] >= 0 && !((fb[u[k] >> 5] >> (u[k] & 31)) & 1u)) u[k] = -1;
-    uint64_t x[4][P];
+    for (int k = 0; k < G; ++k)
+        if (fb && u[k] >= 0 && !((fb[u[k] >> 5] >> (u[k] & 31)) & 1u)) u[k] = -1;
+    uint64_t x[G][P];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < G; ++k) {
         if (u[k] >= 0) load_words<P>(w.vis + (size_t)u[k] * P, x[k]);
         else {
 #pragma unroll
@@ -187,7 +195,7 @@ __device__ __forceinline__ void gather4(const Wave& w, const uint32_t* fb, const
         }
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < G; ++k)
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] |= x[k][s];
 }
@@ -251,7 +259,7 @@ __device__ __forceinline__ bool decide_pull(const Wave& w, const RoundCtl* c) {
 
 // Bits still missing at v over the unfinished slots um.
 template <int P>
-__device__ __forceinline__ uint64_t missing_bits(const uint64_t (&acc)[P], const uint64_t (&vs)[P], const uint64_t (&all)[P],
+__device__ __forceinline__ uint64_t missing_bits(const uint64_t (&acc)[P], const uint64_t (&vs)[P], const uint64_t* all,
                                                  unsigned int um) {
     uint64_t rem = 0;
 #pragma unroll
@@ -261,7 +269,7 @@ __device__ __forceinline__ uint64_t missing_bits(const uint64_t (&acc)[P], const
 }
 
 template <int P>
-__device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], const uint64_t (&all)[P], unsigned int active) {
+__device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], const uint64_t* all, unsigned int active) {
     unsigned int um = 0;
 #pragma unroll
     for (int s = 0; s < P; ++s)
@@ -531,7 +539,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     const bool pull = c->mode != 0;
     // F_round's bitmap (read) and F_{round+1}'s (written by whoever adds a vertex;
     // phase A of this round cleared it)
-    const uint32_t* fb = (round & 1) ? w.fb1 : w.fb0;
+    // a dense frontier (over n/8) passes the membership test almost always: skip it then
+    const uint32_t* fb = (qlen * 8 > (unsigned long long)w.n) ? nullptr : ((round & 1) ? w.fb1 : w.fb0);
     uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
 
     if (!pull) {
@@ -594,9 +603,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     // ---- pull: dense pass over every vertex that can still gain sources
     const unsigned int active = c->slot_active;
     unsigned long long my_cnt = 0, my_sdeg = 0;
-    uint64_t all[P];
-#pragma unroll
-    for (int s = 0; s < P; ++s) all[s] = sall[s];
+    const uint64_t* all = sall;  // ALL of each slot, read from shared memory where needed
     // high-degree vertices: their lists are cut into kBigDeg-arc pieces that
     // all CTAs take from a counter; each piece ORs its part into acc[v]
     for (;;) {
@@ -629,8 +636,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         uint64_t acc[P];
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] = 0;
-        for (int64_t b0 = a0; b0 < a1; b0 += 4 * kThreads) {
-            gather4<P>(w, fb, w.adj, b0 + threadIdx.x, kThreads, a1, acc);
+        for (int64_t b0 = a0; b0 < a1; b0 += Gath<P>::G * kThreads) {
+            gather<P>(w, fb, w.adj, b0 + threadIdx.x, kThreads, a1, acc);
 #pragma unroll
             for (int s = 0; s < P; ++s) {
                 const uint64_t wa = warp_or(acc[s]);
@@ -682,8 +689,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         uint64_t acc[P];
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] = 0;
-        for (int64_t b0 = o0; b0 < o1; b0 += 128) {
-            gather4<P>(w, fb, w.adj, b0 + lane, 32, o1, acc);
+        for (int64_t b0 = o0; b0 < o1; b0 += 32 * Gath<P>::G) {
+            gather<P>(w, fb, w.adj, b0 + lane, 32, o1, acc);
 #pragma unroll
             for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
             if (missing_bits<P>(acc, vs, all, um) == 0) break;
@@ -714,8 +721,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
                 uint64_t acc[P];
 #pragma unroll
                 for (int s = 0; s < P; ++s) acc[s] = 0;
-                for (int64_t e = o0; e < o1; e += 4) {
-                    gather4<P>(w, fb, wadj - lo, e, 1, o1, acc);
+                for (int64_t e = o0; e < o1; e += Gath<P>::G) {
+                    gather<P>(w, fb, wadj - lo, e, 1, o1, acc);
                     if (missing_bits<P>(acc, vs, all, um) == 0) break;
                 }
                 joined = pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
