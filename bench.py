@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-requests", type=int, default=200)
     ap.add_argument("--serve-s", type=float, default=2.0, help="seconds per offered serving load (0: skip)")
+    ap.add_argument("--no-single-compare", dest="single_compare", action="store_false",
+                    help="skip timing the clusters one call each")
     ap.add_argument("--fixed-tune", default="", help="'alpha,slots' instead of the autotuner (profiling runs)")
     return ap.parse_args()
 
@@ -363,6 +365,28 @@ def run_cbfs(args, ws, rank, local):
                               "share_of_traversal": round(e_ms / max(sum(split[k]["ms"] for k in
                                                                         ("setup", "vertex_phase", "edge_phase")), 1e-9), 3)}
 
+    # the same 256 clusters as 256 separate one-cluster calls (cbfs_run) on the same GPU
+    one = None
+    if args.single_compare:
+        d1 = torch.empty(n, dtype=torch.uint8, device=dev)
+        m1 = torch.empty((d, n), dtype=torch.int64, device=dev)
+        for S in clusters:  # warm: every cluster size's graph captured
+            g.run(S, d, d1, m1)
+        for S in clusters:
+            g.run(S, d, d1, m1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for S in clusters:
+            g.run(S, d, d1, m1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        one_ms = e0.elapsed_time(e1)
+        one = {"ms_for_all_clusters": round(one_ms, 3), "gteps": round(src_edges / (one_ms / 1e3) / 1e9, 3),
+               "batched_speedup": round(one_ms / cbfs_step_ms, 3),
+               "mode": "cbfs_run per cluster (its own waves of one slot), same clusters, same GPU"}
+        del d1, m1
+
     # label-query latency: single requests of U{1..65536} pairs, H2D + kernel + D2H each
     lat = []
     rng = np.random.default_rng(rank_seed(rank) + 11)
@@ -394,20 +418,28 @@ def run_cbfs(args, ws, rank, local):
         L60.append(ld, lm, [len(S) for S in lab_clusters])
         del ld, lm
         torch.cuda.synchronize()
-        with QueryServer(L60, max_batch=args.query_batch, slots=4) as srv:
+        serve_batch = 4 * args.query_batch  # one launch may pack several requests
+        # the server, its completion thread and the load generator share one
+        # interpreter: a 0.1 ms GIL switch interval keeps them from waiting 5 ms turns
+        old_switch = sys.getswitchinterval()
+        sys.setswitchinterval(1e-4)
+        with QueryServer(L60, max_batch=serve_batch, slots=4) as srv:
+            # saturation: the same request mix (sizes uniform in 1..65536) offered as fast as possible
             rng = np.random.default_rng(rank_seed(rank) + 13)
-            big = rng.integers(0, n, size=(args.query_batch, 2)).astype(np.int32)
-            for _ in range(4):
-                srv.submit(big).result()  # warm
+            pool = rng.integers(0, n, size=(4 * args.query_batch, 2)).astype(np.int32)
+            sizes = rng.integers(1, args.query_batch + 1, size=3000)
+            starts = rng.integers(0, 3 * args.query_batch + 1, size=3000)
+            for i in range(50):
+                srv.submit(pool[starts[i]:starts[i] + sizes[i]])
             t0 = time.perf_counter()
-            futs = [srv.submit(big) for _ in range(64)]
+            futs = [srv.submit(pool[starts[i]:starts[i] + sizes[i]]) for i in range(50, 3000)]
             for f in futs:
                 f.result()
-            sat_qps = 64 * args.query_batch / (time.perf_counter() - t0)
+            sat_qps = float(sizes[50:].sum()) / (time.perf_counter() - t0)
         loads = {}
         mean_req = (args.query_batch + 1) / 2.0
         for load in (0.5, 0.8):
-            with QueryServer(L60, max_batch=args.query_batch, slots=4) as srv:
+            with QueryServer(L60, max_batch=serve_batch, slots=4) as srv:
                 futs, offered, elapsed = poisson_load(srv, n, rate_rps=load * sat_qps / mean_req,
                                                       duration_s=args.serve_s, max_pairs=args.query_batch,
                                                       seed=rank_seed(rank) + int(load * 100))
@@ -415,8 +447,11 @@ def run_cbfs(args, ws, rank, local):
             loads[f"{load}x"] = {"p50_ms": round(st_["p50_ms"], 4), "p99_ms": round(st_["p99_ms"], 4),
                                  "qps": round(offered / elapsed, 1), "requests": st_["requests"],
                                  "batches": st_["batches"]}
+        sys.setswitchinterval(old_switch)
         serving = {"labels": "60 degree-ordered clusters (Section 4.2 selection), d=2, 1020 B/vertex",
-                   "arrivals": "Poisson, request sizes uniform in 1..65536 pairs", "saturation_qps": round(sat_qps, 1),
+                   "gil_switch_interval_s": 1e-4,
+                   "arrivals": "Poisson, request sizes uniform in 1..65536 pairs",
+                   "saturation_qps": round(sat_qps, 1), "max_batch_pairs": serve_batch,
                    "offered": loads}
         del L60
 
@@ -431,28 +466,36 @@ def run_cbfs(args, ws, rank, local):
         bo = dist_h.numel() + masks_h.numel() * 8 + args.query_batch * 2
         del dist, masks
         torch.cuda.empty_cache()
-        e_times = []
+        e_times, parts = [], []
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             g2 = cbfs.Graph(off_pin, adj_pin, validate=True)
+            t1 = time.perf_counter()
             dd, mm = g2.run_batched(None, d, tune=tset, sources_concat=src_cat, cluster_off=coff)
+            t2 = time.perf_counter()
             L.reset()
             L.append(dd, mm, ks)
             pairs_dev.copy_(pin_pairs, non_blocking=True)
             L.query(pairs_dev, out=answers)
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
             dist_h.copy_(dd, non_blocking=True)
             masks_h.copy_(mm, non_blocking=True)
             pin_ans.copy_(answers, non_blocking=True)
             torch.cuda.synchronize()
-            e_times.append(time.perf_counter() - t0)
+            t4 = time.perf_counter()
+            e_times.append(t4 - t0)
+            parts.append((t1 - t0, t2 - t1, t3 - t2, t4 - t3))
             g2.close()
             del dd, mm
         e_t = max(statistics.median(e_times), 1e-9)
         e2e = {"value": round(src_edges / e_t / 1e9 * ws, 4), "unit": "GTEPS", "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(bo), "ms_per_step": round(e_t * 1e3, 3),
                "includes": "graph create+validate from pinned host CSR, batched C-BFS, label append, query, "
-                           "D2H of dist/masks/answers"}
+                           "D2H of dist/masks/answers",
+               "ms_parts": dict(zip(("graph_create", "traversal", "labels_query", "d2h"),
+                                    [round(1e3 * statistics.median(p[i] for p in parts), 2) for i in range(4)]))}
 
     if rank == 0:
         line = {
@@ -475,6 +518,7 @@ def run_cbfs(args, ws, rank, local):
             "kernel_ms_one_untimed_step": {k: split[k] for k in ("setup", "vertex_phase", "edge_phase")},
             "query": query,
             "serving": serving,
+            "one_cluster_per_launch": one,
         }
         print(json.dumps(line), flush=True)
     if pg:

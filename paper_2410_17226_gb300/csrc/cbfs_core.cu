@@ -324,7 +324,13 @@ __global__ void k_seed(Wave w, const uint64_t* seeds, int count) {
 // After a wave: every source must have seen every source of its cluster.
 // Otherwise the cluster is not connected within distance d and the implied
 // last subset S_v[d] would be wrong, so the call fails with CBFS_E_DIAMETER.
-__global__ void k_check_sources(Wave w, const uint64_t* seeds, int count) {
+// bound_round > 0: the wave ran exactly bound_round rounds without looking;
+// if its frontier was still not empty it is flagged for a rerun instead.
+__global__ void k_check_sources(Wave w, const uint64_t* seeds, int count, int bound_round, int* unfinished) {
+    if (bound_round > 0 && w.ctl[bound_round].qlen != 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *unfinished = 1;
+        return;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const uint64_t e = seeds[i];
         const int s = (int)((e >> 40) & 0xFF);
@@ -965,6 +971,8 @@ struct cbfs_graph_s {
     };
     std::vector<GraphEntry> graphs;  // most recently used last
     std::vector<uint64_t> seen;      // call shapes run once (host-driven) and not yet captured
+    int* wave_flags = nullptr;       // host-driven: waves that needed more rounds than enqueued
+    int64_t wave_flags_cap = 0;
 };
 
 namespace {
@@ -1201,7 +1209,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         if (e == cudaSuccess) e = eb;
         if (e != cudaSuccess) break;
         if ((e = launch_round(w, 0, grid, cs, 2, g->iperm_d)) != cudaSuccess) break;
-        k_check_sources<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt);
+        k_check_sources<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt, 0, nullptr);
         e = cudaGetLastError();
     }
     cudaGraph_t graph = nullptr;
@@ -1384,10 +1392,17 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
         }
     }
 
-    for (int wv = 0; wv < nwaves; ++wv) {
+    // Host-driven rounds.  A "careful" wave synchronises every two rounds to
+    // see its frontier; it tells how many rounds waves of this call take.  The
+    // following waves enqueue that many rounds plus a margin without waiting
+    // (rounds past the end return at once) and flag themselves when their
+    // frontier was still not empty; flagged waves are run carefully again.
+    rc = ensure_dev(&g->wave_flags, &g->wave_flags_cap, nwaves);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(g->wave_flags, 0, sizeof(int) * (size_t)nwaves, st));
+    auto run_wave = [&](int wv, int bound, int* rounds_out) -> int {
         const int c0 = wv * P;
-        const int nsl = std::min(P, C - c0);
-        w.nslots = nsl;
+        w.nslots = std::min(P, C - c0);
         w.slots = g->slots + (size_t)wv * P;
         CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
@@ -1401,32 +1416,70 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
         k_seed<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
         prof_end(g, ev, st);
         CK(cudaGetLastError());
-        bool done = false;
-        for (int r = 0; r < kMaxRounds - 1 && !done; ++r) {
-            ev = prof_begin(g, 1, st);
-            CK(launch_round(w, r, grid, st, 0));
-            prof_end(g, ev, st);
-            ev = prof_begin(g, 2, st);
-            CK(launch_round(w, r, grid, st, 1));
-            prof_end(g, ev, st);
-            CK(cudaMemcpyAsync(&g->h_q[r + 1], &g->ctl[r + 1].qlen, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-            if (r % 2 == 1 || r == kMaxRounds - 2) {
-                CK(cudaStreamSynchronize(st));
-                if (g->h_q[r] == 0 || g->h_q[r + 1] == 0) done = true;
+        int rounds = 0;
+        if (bound > 0) {
+            for (int r = 0; r < bound; ++r) {
+                ev = prof_begin(g, 1, st);
+                CK(launch_round(w, r, grid, st, 0));
+                prof_end(g, ev, st);
+                ev = prof_begin(g, 2, st);
+                CK(launch_round(w, r, grid, st, 1));
+                prof_end(g, ev, st);
             }
-        }
-        if (!done) {
-            CK(cudaStreamSynchronize(st));
-            prof_collect(g);
-            return CBFS_E_DEPTH;
+            rounds = bound;
+        } else {
+            bool done = false;
+            for (int r = 0; r < kMaxRounds - 1 && !done; ++r) {
+                ev = prof_begin(g, 1, st);
+                CK(launch_round(w, r, grid, st, 0));
+                prof_end(g, ev, st);
+                ev = prof_begin(g, 2, st);
+                CK(launch_round(w, r, grid, st, 1));
+                prof_end(g, ev, st);
+                CK(cudaMemcpyAsync(&g->h_q[r + 1], &g->ctl[r + 1].qlen, sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, st));
+                if (r % 2 == 1 || r == kMaxRounds - 2) {
+                    CK(cudaStreamSynchronize(st));
+                    if (g->h_q[r] == 0 || g->h_q[r + 1] == 0) done = true;
+                }
+                rounds = r + 1;
+            }
+            if (!done) {
+                CK(cudaStreamSynchronize(st));
+                prof_collect(g);
+                return CBFS_E_DEPTH;
+            }
         }
         ev = prof_begin(g, 0, st);
         CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
         prof_end(g, ev, st);
         ev = prof_begin(g, 0, st);
-        k_check_sources<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
+        k_check_sources<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt, bound, g->wave_flags + wv);
         prof_end(g, ev, st);
         CK(cudaGetLastError());
+        *rounds_out = rounds;
+        return CBFS_OK;
+    };
+    int est = 0;
+    bool any_optimistic = false;
+    for (int wv = 0; wv < nwaves; ++wv) {
+        const int bound = est > 0 ? std::min(est + 2, kMaxRounds - 1) : 0;
+        int used = 0;
+        rc = run_wave(wv, bound, &used);
+        if (rc) return rc;
+        if (bound == 0) est = used;
+        else any_optimistic = true;
+    }
+    if (any_optimistic) {
+        std::vector<int> flags((size_t)nwaves, 0);
+        CK(cudaMemcpyAsync(flags.data(), g->wave_flags, sizeof(int) * (size_t)nwaves, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int wv = 0; wv < nwaves; ++wv) {
+            if (!flags[wv]) continue;
+            int used = 0;
+            rc = run_wave(wv, 0, &used);
+            if (rc) return rc;
+        }
     }
     int status = 0;
     CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1635,6 +1688,7 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     if (g->cap_stream2) cudaStreamDestroy(g->cap_stream2);
     dev_free(g->round_dev);
     dev_free(g->iters);
+    dev_free(g->wave_flags);
     if (g->h_q) cudaFreeHost(g->h_q);
     if (g->h_slots) cudaFreeHost(g->h_slots);
     if (g->h_seeds) cudaFreeHost(g->h_seeds);

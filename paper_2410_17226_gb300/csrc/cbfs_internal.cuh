@@ -127,7 +127,7 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 
 // Traversal kernels (cbfs_core.cu).  seeds[i] = slot << 40 | j << 32 | vertex.
 __global__ void k_seed(Wave w, const uint64_t* seeds, int count);
-__global__ void k_check_sources(Wave w, const uint64_t* seeds, int count);
+__global__ void k_check_sources(Wave w, const uint64_t* seeds, int count, int bound_round, int* unfinished);
 template <int P>
 __global__ void k_phase_a(Wave w, int round);
 template <int P>

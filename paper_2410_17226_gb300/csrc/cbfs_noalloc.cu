@@ -182,7 +182,7 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
         }
     }
     if (!done) return CBFS_E_DEPTH;
-    k_check_sources<<<1, kThreads, 0, st>>>(w, d_seeds, k);
+    k_check_sources<<<1, kThreads, 0, st>>>(w, d_seeds, k, 0, nullptr);
     NA_CK(cudaGetLastError());
     int status = 0;
     NA_CK(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -128,6 +128,20 @@ def test_graph_replay_with_new_sources_each_call(cb):
             assert (bd[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(bm[c]) == om).all(), (seed, c)
 
 
+def test_host_loop_reruns_waves_deeper_than_the_first(cb):
+    """Host-driven rounds: waves after the first enqueue about as many rounds
+    as the first needed; a deeper wave is detected and traversed again."""
+    off, adj = I.path(240)
+    g = cb.Graph(off, adj)
+    clusters = [np.array([120, 121], np.int32), np.array([0, 1], np.int32), np.array([60], np.int32),
+                np.array([239, 238], np.int32)]
+    for tune in ({"slots": 1, "host_loop": 1}, {"slots": 2, "host_loop": 1}):
+        bd, bm = g.run_batched(clusters, 2, tune=tune)
+        for c, S in enumerate(clusters):
+            od, om = O.cbfs_alg1(off, adj, S, 2)
+            assert (bd[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(bm[c]) == om).all(), (tune, c)
+
+
 def test_hubs_and_big_lists(cb):
     # a star with 10000 leaves plus a path hanging off it: hub lists go
     # through the big-list pieces in push and the CTA-per-vertex pull
