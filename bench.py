@@ -419,11 +419,8 @@ def run_cbfs(args, ws, rank, local):
         del ld, lm
         torch.cuda.synchronize()
         serve_batch = 4 * args.query_batch  # one launch may pack several requests
-        # the server, its completion thread and the load generator share one
-        # interpreter: a 0.1 ms GIL switch interval keeps them from waiting 5 ms turns
-        old_switch = sys.getswitchinterval()
-        sys.setswitchinterval(1e-4)
-        with QueryServer(L60, max_batch=serve_batch, slots=4) as srv:
+        sopt = {"pause_gc": True, "switch_interval_s": 1e-4}
+        with QueryServer(L60, max_batch=serve_batch, slots=4, **sopt) as srv:
             # saturation: the same request mix (sizes uniform in 1..65536) offered as fast as possible
             rng = np.random.default_rng(rank_seed(rank) + 13)
             pool = rng.integers(0, n, size=(4 * args.query_batch, 2)).astype(np.int32)
@@ -439,7 +436,7 @@ def run_cbfs(args, ws, rank, local):
         loads = {}
         mean_req = (args.query_batch + 1) / 2.0
         for load in (0.5, 0.8):
-            with QueryServer(L60, max_batch=serve_batch, slots=4) as srv:
+            with QueryServer(L60, max_batch=serve_batch, slots=4, **sopt) as srv:
                 futs, offered, elapsed = poisson_load(srv, n, rate_rps=load * sat_qps / mean_req,
                                                       duration_s=args.serve_s, max_pairs=args.query_batch,
                                                       seed=rank_seed(rank) + int(load * 100))
@@ -447,9 +444,8 @@ def run_cbfs(args, ws, rank, local):
             loads[f"{load}x"] = {"p50_ms": round(st_["p50_ms"], 4), "p99_ms": round(st_["p99_ms"], 4),
                                  "qps": round(offered / elapsed, 1), "requests": st_["requests"],
                                  "batches": st_["batches"]}
-        sys.setswitchinterval(old_switch)
         serving = {"labels": "60 degree-ordered clusters (Section 4.2 selection), d=2, 1020 B/vertex",
-                   "gil_switch_interval_s": 1e-4,
+                   "server_options": sopt,
                    "arrivals": "Poisson, request sizes uniform in 1..65536 pairs",
                    "saturation_qps": round(sat_qps, 1), "max_batch_pairs": serve_batch,
                    "offered": loads}

@@ -22,6 +22,8 @@ is in flight: every pair is answered independently by the same kernel.
 from __future__ import annotations
 
 import collections
+import gc
+import sys
 import threading
 import time
 from concurrent.futures import Future
@@ -63,7 +65,20 @@ class _Slot:
 
 class QueryServer:
     def __init__(self, labels: "cbfs.Labels", max_batch: int = 65536, slots: int = 4,
-                 memory_budget_bytes: int | None = None, device=None):
+                 memory_budget_bytes: int | None = None, device=None, pause_gc: bool = False,
+                 switch_interval_s: float | None = None):
+        """``pause_gc`` disables Python's cyclic garbage collector while the
+        server runs (its pauses over many live requests were the latency
+        tail); ``switch_interval_s`` shortens the interpreter's thread switch
+        interval so the scheduler and completion threads do not wait 5 ms
+        turns.  Both are process-wide settings, restored by ``close``."""
+        self._gc_was_enabled = gc.isenabled()
+        self._old_switch = sys.getswitchinterval()
+        self._pause_gc = pause_gc
+        if pause_gc:
+            gc.disable()
+        if switch_interval_s:
+            sys.setswitchinterval(switch_interval_s)
         self.labels = labels
         self.max_batch = int(max_batch)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -107,6 +122,9 @@ class QueryServer:
             self._cv.notify_all()
         self._sched.join()
         self._compl.join()
+        sys.setswitchinterval(self._old_switch)
+        if self._pause_gc and self._gc_was_enabled:
+            gc.enable()
 
     def __enter__(self):
         return self

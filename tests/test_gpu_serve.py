@@ -87,9 +87,23 @@ def test_poisson_load_reports_latency(setup):
     cbfs, g, L, dist, masks, ks = setup
     from paper_2410_17226_gb300.serve import QueryServer, poisson_load
 
-    with QueryServer(L, max_batch=4096, slots=3) as srv:
+    with QueryServer(L, max_batch=4096, slots=3, pause_gc=True, switch_interval_s=1e-4) as srv:
         futs, offered, elapsed = poisson_load(srv, g.n, rate_rps=400.0, duration_s=0.5, max_pairs=2000, seed=5)
         st = srv.stats()
     assert st["requests"] == len(futs)
     assert st["pairs"] == offered
     assert st["p99_ms"] >= st["p50_ms"] >= 0
+
+
+def test_server_restores_interpreter_settings(setup):
+    import gc
+    import sys
+
+    cbfs, g, L, dist, masks, ks = setup
+    from paper_2410_17226_gb300.serve import QueryServer
+
+    before = (gc.isenabled(), sys.getswitchinterval())
+    with QueryServer(L, max_batch=256, slots=1, pause_gc=True, switch_interval_s=2e-4) as srv:
+        assert not gc.isenabled() and abs(sys.getswitchinterval() - 2e-4) < 1e-9
+        srv.submit(np.zeros((3, 2), np.int32)).result()
+    assert (gc.isenabled(), sys.getswitchinterval()) == before
