@@ -44,7 +44,7 @@ VERTEX_BYTES = 41   # per frontier appearance: 8 B offsets + 33 B vertex-phase r
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["cbfs", "reference"], default="cbfs")
     ap.add_argument("--scale", type=int, default=22)
