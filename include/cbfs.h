@@ -94,8 +94,11 @@ typedef struct cbfs_cluster_stats_s {
  * adj is int32 vertex ids.  inputs_on_device selects whether off/adj are
  * device or host pointers; the caller keeps ownership of them and may free
  * them when the call returns.  validate != 0 checks the graph (see
- * CBFS_E_GRAPH) on the device before returning.  The call synchronises
- * `stream`.  Limits: 0 <= n < 2^31, 0 <= nnz < 2^40.
+ * CBFS_E_GRAPH) on the device before returning.  Offsets that do not start
+ * at 0, end at nnz and never decrease always give CBFS_E_GRAPH.  All work
+ * after the copies (checks, degree order, relabelled copy) runs on the
+ * device.  The call synchronises `stream`.  Limits: 0 <= n < 2^31,
+ * 0 <= nnz < 2^40, every degree < 2^31.
  * Problem statement: Section 2 (unweighted graph G = (V, E)).
  */
 int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t* adj, int64_t nnz,
@@ -109,7 +112,8 @@ int cbfs_graph_info(cbfs_graph_t g, int64_t* host_n, int64_t* host_nnz);
 
 /*
  * One C-BFS (Algorithm 1, Section 3.2) from the k sources host_sources[0..k)
- * with cluster diameter bound d.  Writes dist[n] and masks[d][n] (device).
+ * with cluster diameter bound d.  Writes dist[n] and masks[d][n], in device
+ * or host memory (see cbfs_run_batched).
  * Sources must be distinct and in [0, n); 1 <= k <= 64; 0 <= d <= 15.  d must
  * bound the pairwise source distances, otherwise CBFS_E_DIAMETER is returned
  * (the library detects the violation rather than producing wrong subsets).
@@ -127,9 +131,31 @@ int cbfs_run(cbfs_graph_t g, const int32_t* host_sources, int k, int d, uint8_t*
  * round's launches (no paper counterpart: the paper runs clusters one after
  * another, Algorithm "Framework of Landmark Labeling").  tune may be NULL.
  * Same validation, errors and completion rule as cbfs_run.
+ *
+ * dist and masks may be device memory (written by the kernels) or host
+ * memory.  With host memory every wave's outputs go to a device buffer and
+ * are copied out on a second stream while the next wave traverses; pinned
+ * memory (cudaHostAlloc / cudaHostRegister) lets the copies overlap,
+ * pageable memory is correct but each copy blocks the calling thread.
+ * Either way the outputs are complete when the call returns.
  */
 int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const int32_t* host_cluster_off,
                      int C, int d, uint8_t* dist, uint64_t* masks, const cbfs_tune_t* tune, void* stream);
+
+/*
+ * cbfs_run_batched that also appends the C clusters, in order, to the label
+ * store `labels` (created with this graph's n and the same d): the rows of
+ * the landmark labeling (Section 4.2) are written from each wave's outputs
+ * while they are still on the device, so building labels costs no second
+ * pass over dist/masks.  dist and masks may both be NULL (labels only), or
+ * device or host memory as in cbfs_run_batched.  CBFS_E_NOMEM when the
+ * store has no room for C more clusters, CBFS_E_INVALID when its n or d
+ * differ; on any error the store's count is left as it was.  Always driven
+ * from the host (no CUDA-graph replay).
+ */
+int cbfs_run_batched_labels(cbfs_graph_t g, const int32_t* host_sources_concat, const int32_t* host_cluster_off,
+                            int C, int d, uint8_t* dist, uint64_t* masks, cbfs_labels_t labels,
+                            const cbfs_tune_t* tune, void* stream);
 
 /*
  * cbfs_run without any allocation.  The paper has no counterpart: this entry

@@ -62,6 +62,7 @@ SIGNATURES = {
     "cbfs_graph_info": (_I, [_P, _P, _P]),
     "cbfs_run": (_I, [_P, _P, _I, _I, _P, _P, _P]),
     "cbfs_run_batched": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P]),
+    "cbfs_run_batched_labels": (_I, [_P, _P, _P, _I, _I, _P, _P, _P, _P, _P]),
     "cbfs_run_noalloc": (_I, [_I64, _P, _P, _I64, _P, _I, _I, _P, _P, _P]),
     "cbfs_output_stats": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
     "cbfs_profile": (_I, [_P, _I, _P]),
@@ -195,36 +196,65 @@ class Graph:
         _check(rc, "cbfs_run")
         return dist, masks
 
-    def run_batched(self, clusters: Sequence | None, d: int, dist: torch.Tensor | None = None,
-                    masks: torch.Tensor | None = None, tune: dict | None = None, stream=None,
-                    sources_concat=None, cluster_off=None):
-        """C clusters in one call (``cbfs_run_batched``).  ``clusters`` is a list
-        of source arrays; alternatively pass ``sources_concat`` and
-        ``cluster_off`` (the C ABI's layout) with ``clusters=None``.  Returns
-        ``(dist uint8[C, n], masks int64[C, d, n])``."""
+    @staticmethod
+    def _cluster_layout(clusters, sources_concat, cluster_off):
         if clusters is None:
-            src, coff = _host_i32(sources_concat), _host_i32(cluster_off)
-        else:
-            arrs = [_host_i32(c) for c in clusters]
-            coff = np.zeros(len(arrs) + 1, dtype=np.int32)
-            np.cumsum([a.size for a in arrs], out=coff[1:])
-            src = np.concatenate(arrs).astype(np.int32) if arrs else np.zeros(0, np.int32)
-        C = coff.size - 1
-        dev = torch.device("cuda", torch.cuda.current_device())
-        if dist is None:
-            dist = torch.empty((C, self.n), dtype=torch.uint8, device=dev)
-        if masks is None:
-            masks = torch.empty((C, max(d, 0), self.n), dtype=torch.int64, device=dev)
+            return _host_i32(sources_concat), _host_i32(cluster_off)
+        arrs = [_host_i32(c) for c in clusters]
+        coff = np.zeros(len(arrs) + 1, dtype=np.int32)
+        np.cumsum([a.size for a in arrs], out=coff[1:])
+        src = np.concatenate(arrs).astype(np.int32) if arrs else np.zeros(0, np.int32)
+        return src, coff
+
+    @staticmethod
+    def _tune(tune: dict | None) -> "Tune":
         t = Tune()
         if tune:
             t.pull_alpha = float(tune.get("pull_alpha", 0.0))
             t.slots = int(tune.get("slots", 0))
             t.dense_div = int(tune.get("dense_div", 0))
             t.host_loop = int(tune.get("host_loop", 0))
+        return t
+
+    def run_batched(self, clusters: Sequence | None, d: int, dist: torch.Tensor | None = None,
+                    masks: torch.Tensor | None = None, tune: dict | None = None, stream=None,
+                    sources_concat=None, cluster_off=None):
+        """C clusters in one call (``cbfs_run_batched``).  ``clusters`` is a list
+        of source arrays; alternatively pass ``sources_concat`` and
+        ``cluster_off`` (the C ABI's layout) with ``clusters=None``.  ``dist``
+        and ``masks`` may be CUDA tensors or host tensors (pinned ones let the
+        copies overlap the traversal).  Returns ``(dist uint8[C, n],
+        masks int64[C, d, n])``, allocated on the GPU when not given."""
+        src, coff = self._cluster_layout(clusters, sources_concat, cluster_off)
+        C = coff.size - 1
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if dist is None:
+            dist = torch.empty((C, self.n), dtype=torch.uint8, device=dev)
+        if masks is None:
+            masks = torch.empty((C, max(d, 0), self.n), dtype=torch.int64, device=dev)
+        t = self._tune(tune)
         src_p = src.ctypes.data if src.size else np.zeros(1, np.int32).ctypes.data
         rc = lib().cbfs_run_batched(self._h, src_p, coff.ctypes.data, int(C), int(d), _ptr(dist),
                                     _ptr(masks) if d > 0 else None, ctypes.byref(t), _stream_ptr(stream))
         _check(rc, "cbfs_run_batched")
+        return dist, masks
+
+    def run_batched_labels(self, clusters: Sequence | None, d: int, labels: "Labels", dist: torch.Tensor | None = None,
+                           masks: torch.Tensor | None = None, tune: dict | None = None, stream=None,
+                           sources_concat=None, cluster_off=None):
+        """``cbfs_run_batched_labels``: the batched traversal that also appends
+        every cluster to ``labels`` from the device-side wave outputs.
+        ``dist``/``masks`` are optional (None = labels only) and may be CUDA
+        or host tensors."""
+        src, coff = self._cluster_layout(clusters, sources_concat, cluster_off)
+        C = coff.size - 1
+        t = self._tune(tune)
+        src_p = src.ctypes.data if src.size else np.zeros(1, np.int32).ctypes.data
+        rc = lib().cbfs_run_batched_labels(self._h, src_p, coff.ctypes.data, int(C), int(d),
+                                           _ptr(dist) if dist is not None else None,
+                                           _ptr(masks) if (masks is not None and d > 0) else None, labels._h,
+                                           ctypes.byref(t), _stream_ptr(stream))
+        _check(rc, "cbfs_run_batched_labels")
         return dist, masks
 
     def profile(self, enable: bool) -> dict:

@@ -912,7 +912,6 @@ struct cbfs_graph_s {
     int32_t* adj_r = nullptr;
     int32_t* perm = nullptr;   // rank -> caller's id
     int32_t* iperm_d = nullptr;  // caller's id -> rank (device, for the output emit)
-    std::vector<int32_t> iperm;  // caller's id -> rank (host, for the sources)
     uint8_t* dist_r = nullptr;   // internal output rows of a wave
     uint64_t* masks_r = nullptr;
     int64_t masks_r_cap = 0;
@@ -973,6 +972,13 @@ struct cbfs_graph_s {
     std::vector<uint64_t> seen;      // call shapes run once (host-driven) and not yet captured
     int* wave_flags = nullptr;       // host-driven: waves that needed more rounds than enqueued
     int64_t wave_flags_cap = 0;
+    // staged outputs (host destinations or a label store): two wave buffers,
+    // copied out on copy_stream while the next wave traverses
+    uint8_t* stage = nullptr;
+    int64_t stage_cap = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_emit[2] = {nullptr, nullptr};
+    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -1237,12 +1243,40 @@ int slots_for(const cbfs_tune_t* tune, int C) {
     return p2;
 }
 
+// True when p is host memory (pinned or pageable): kernels do not write it.
+bool is_host_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged;
+}
+
+int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C, int d, uint8_t* dist,
+                       uint64_t* masks, cbfs_labels_s* L, int lbase, const cbfs_tune_t* tune, cudaStream_t st);
+
+// Outputs go to dist/masks (device or host memory, either may be null when
+// L is given) and, when L is not null, are appended to the label store.
 int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C, int d, uint8_t* dist,
-                 uint64_t* masks, const cbfs_tune_t* tune, cudaStream_t st) {
+                 uint64_t* masks, cbfs_labels_s* L, const cbfs_tune_t* tune, cudaStream_t st) {
     int rc = check_clusters(g, src, coff, C, d);
     if (rc) return rc;
     if (C == 0) return CBFS_OK;
     CK(cudaSetDevice(g->device));
+    int lbase = 0;
+    if (L) {
+        rc = labels_reserve(L, g->n, d, coff, C, &lbase);
+        if (rc) return rc;
+    }
+    rc = run_clusters_inner(g, src, coff, C, d, dist, masks, L, lbase, tune, st);
+    if (rc && L) labels_rollback(L, lbase);
+    return rc;
+}
+
+int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C, int d, uint8_t* dist,
+                       uint64_t* masks, cbfs_labels_s* L, int lbase, const cbfs_tune_t* tune, cudaStream_t st) {
+    int rc = CBFS_OK;
     const int P = slots_for(tune, C);
     float alpha = 0.02f;
     if (tune && tune->pull_alpha != 0.f) alpha = tune->pull_alpha;
@@ -1254,6 +1288,22 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     const int grid = g->grid_p[P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3];
     const int nwaves = (C + P - 1) / P;
     const int64_t total_src = coff[C];
+    // staged mode: every wave emits into one of two device buffers of P
+    // clusters, [dist P x n | masks P x d x n], then copies out / appends
+    const bool staged = L || (dist && is_host_pointer(dist)) || (masks && is_host_pointer(masks));
+    const int64_t stage_dist_bytes = ((int64_t)P * g->n + 255) / 256 * 256;
+    const int64_t stage_slot = stage_dist_bytes + (int64_t)P * d * g->n * 8;
+    if (staged) {
+        rc = ensure_dev(&g->stage, &g->stage_cap, 2 * stage_slot);
+        if (rc) return rc;
+        if (!g->copy_stream) {
+            CK(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+            for (int b = 0; b < 2; ++b) {
+                CK(cudaEventCreateWithFlags(&g->ev_emit[b], cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&g->ev_copy[b], cudaEventDisableTiming));
+            }
+        }
+    }
     rc = ensure_dev(&g->slots, &g->slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_pinned(&g->h_slots, &g->h_slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_dev(&g->seeds, &g->seeds_cap, total_src);
@@ -1271,12 +1321,19 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
             memset(&sd, 0, sizeof(sd));
             if (c < C) {
                 const int k = coff[c + 1] - coff[c];
-                sd.dist = dist + (size_t)c * (size_t)n;
-                sd.masks = d ? masks + (size_t)c * (size_t)d * (size_t)n : nullptr;
+                if (staged) {
+                    uint8_t* base = g->stage + (size_t)(wv % 2) * (size_t)stage_slot;
+                    sd.dist = base + (size_t)s * (size_t)n;
+                    sd.masks = d ? reinterpret_cast<uint64_t*>(base + stage_dist_bytes) + (size_t)s * (size_t)d * (size_t)n
+                                 : nullptr;
+                } else {
+                    sd.dist = dist + (size_t)c * (size_t)n;
+                    sd.masks = d ? masks + (size_t)c * (size_t)d * (size_t)n : nullptr;
+                }
                 sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
                 sd.cluster = c;
                 for (int j = 0; j < k; ++j)
-                    g->h_seeds[ns++] = ((uint64_t)s << 40) | ((uint64_t)j << 32) | (uint32_t)g->iperm[src[coff[c] + j]];
+                    g->h_seeds[ns++] = ((uint64_t)s << 40) | ((uint64_t)j << 32) | (uint32_t)src[coff[c] + j];  // mapped to ranks on the device
             }
             g->h_slots[(size_t)wv * P + s] = sd;
         }
@@ -1285,6 +1342,7 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     CK(cudaMemcpyAsync(g->slots, g->h_slots, sizeof(SlotDesc) * (size_t)nwaves * P, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(g->seeds, g->h_seeds, sizeof(uint64_t) * (size_t)std::max<int64_t>(ns, 1),
                        cudaMemcpyHostToDevice, st));
+    CK(map_seeds(g->seeds, ns, g->iperm_d, st));
     CK(cudaMemsetAsync(g->status, 0, sizeof(int), st));
 
     Wave w;
@@ -1331,7 +1389,7 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     // Graph mode: a call shape seen before runs as one cached CUDA graph whose
     // rounds loop on the device; a first sighting runs host-driven below and
     // is remembered, so one-off calls (a fresh handle) pay no capture.
-    if (!g->timing && !(tune && tune->host_loop)) {
+    if (!g->timing && !(tune && tune->host_loop) && !staged) {
         if (!g->round_dev) {
             rc = dev_alloc(&g->round_dev, 1);
             if (!rc) rc = dev_alloc(&g->iters, 1);
@@ -1450,9 +1508,28 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
                 return CBFS_E_DEPTH;
             }
         }
+        const int b = wv % 2;
+        if (staged) CK(cudaStreamWaitEvent(st, g->ev_copy[b], 0));  // buffer b copied out by wave wv - 2
         ev = prof_begin(g, 0, st);
         CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
         prof_end(g, ev, st);
+        if (staged) {
+            const uint8_t* sdist = g->stage + (size_t)b * (size_t)stage_slot;
+            const uint64_t* smasks = reinterpret_cast<const uint64_t*>(sdist + stage_dist_bytes);
+            if (dist || masks) {
+                CK(cudaEventRecord(g->ev_emit[b], st));
+                CK(cudaStreamWaitEvent(g->copy_stream, g->ev_emit[b], 0));
+                if (dist)
+                    CK(cudaMemcpyAsync(dist + (size_t)c0 * (size_t)n, sdist, (size_t)w.nslots * (size_t)n, cudaMemcpyDefault,
+                                       g->copy_stream));
+                if (masks && d)
+                    CK(cudaMemcpyAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, smasks,
+                                       sizeof(uint64_t) * (size_t)w.nslots * (size_t)d * (size_t)n, cudaMemcpyDefault,
+                                       g->copy_stream));
+                CK(cudaEventRecord(g->ev_copy[b], g->copy_stream));
+            }
+            if (L) CK(labels_write(L, sdist, smasks, w.nslots, lbase + c0, st));
+        }
         ev = prof_begin(g, 0, st);
         k_check_sources<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt, bound, g->wave_flags + wv);
         prof_end(g, ev, st);
@@ -1480,6 +1557,10 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
             rc = run_wave(wv, 0, &used);
             if (rc) return rc;
         }
+    }
+    if (staged && (dist || masks)) {
+        CK(cudaStreamWaitEvent(st, g->ev_copy[0], 0));
+        CK(cudaStreamWaitEvent(st, g->ev_copy[1], 0));
     }
     int status = 0;
     CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1514,67 +1595,69 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     if (!off || (nnz > 0 && !adj)) return CBFS_E_INVALID;
     if (!off_is_i64 && nnz > 0x7fffffffLL) return CBFS_E_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
-    // host copy of the offsets (degree classes and capacity planning)
-    std::vector<int64_t> h_off((size_t)n + 1);
-    if (off_is_i64) {
-        if (inputs_on_device) CK(cudaMemcpy(h_off.data(), off, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyDeviceToHost));
-        else memcpy(h_off.data(), off, sizeof(int64_t) * (size_t)(n + 1));
-    } else {
-        std::vector<int32_t> o32((size_t)n + 1);
-        if (inputs_on_device) CK(cudaMemcpy(o32.data(), off, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyDeviceToHost));
-        else memcpy(o32.data(), off, sizeof(int32_t) * (size_t)(n + 1));
-        for (int64_t v = 0; v <= n; ++v) h_off[v] = o32[v];
-    }
-    if (h_off[0] != 0 || h_off[n] != nnz) return CBFS_E_GRAPH;
-    for (int64_t v = 0; v < n; ++v)
-        if (h_off[v + 1] < h_off[v]) return CBFS_E_GRAPH;
-
     cbfs_graph_s* g = new (std::nothrow) cbfs_graph_s();
     if (!g) return CBFS_E_NOMEM;
-    int rc = CBFS_OK;
+    int64_t* scratch = nullptr;
+    int32_t* off32 = nullptr;
+    DegreeStats* d_stats = nullptr;
     auto fail = [&](int code) {
+        cudaStreamSynchronize(st);
+        dev_free(scratch);
+        dev_free(off32);
+        dev_free(d_stats);
         cbfs_graph_destroy(g);
         return code;
     };
     cudaGetDevice(&g->device);
     g->n = n;
     g->nnz = nnz;
-    rc = dev_alloc(&g->off, n + 1);
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    sms = std::max(1, sms);
+    int rc = dev_alloc(&g->off, n + 1);
     if (!rc) rc = dev_alloc(&g->adj, nnz);
     if (!rc) rc = dev_alloc(&g->ctl, kMaxRounds);
     if (!rc) rc = dev_alloc(&g->status, 1);
+    if (!rc) rc = dev_alloc(&d_stats, 1);
+    if (!rc) rc = dev_alloc(&scratch, rank_scratch_words(n));
+    if (!rc) rc = dev_alloc(&g->perm, n);
+    if (!rc) rc = dev_alloc(&g->iperm_d, n);
+    if (!rc) rc = dev_alloc(&g->off_r, n + 1);
+    if (!rc) rc = dev_alloc(&g->adj_r, nnz);
     if (rc) return fail(rc);
     if (cudaMallocHost((void**)&g->h_q, sizeof(unsigned long long) * (kMaxRounds + 2)) != cudaSuccess) {
         g->h_q = nullptr;
         return fail(CBFS_E_NOMEM);
     }
-    if (cudaMemcpyAsync(g->off, h_off.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return fail(CBFS_E_CUDA);
-    if (nnz > 0 && cudaMemcpyAsync(g->adj, adj, sizeof(int32_t) * (size_t)nnz,
-                                   inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return fail(CBFS_E_CUDA);
-    // degree classes (caller's ids) for validation, capacity of the push big list
-    std::vector<int32_t> ls, lm, lb;
-    for (int64_t v = 0; v < n; ++v) {
-        const int64_t dg = h_off[v + 1] - h_off[v];
-        if (dg == 0) continue;
-        if (dg <= kPullSmall) ls.push_back((int32_t)v);
-        else if (dg <= kPullMid) lm.push_back((int32_t)v);
-        else lb.push_back((int32_t)v);
-        if (dg > kBigDeg) {
-            g->big_vertices += 1;
-            g->big_pieces += (dg + kBigDeg - 1) / kBigDeg;
-        }
+    // the caller's CSR, offsets widened to int64 on the device
+    cudaError_t e = cudaSuccess;
+    const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (off_is_i64) {
+        e = cudaMemcpyAsync(g->off, off, sizeof(int64_t) * (size_t)(n + 1), kind, st);
+    } else if (inputs_on_device) {
+        e = widen_offsets((const int32_t*)off, g->off, n + 1, sms, st);
+    } else {
+        if (dev_alloc(&off32, n + 1)) return fail(CBFS_E_NOMEM);
+        e = cudaMemcpyAsync(off32, off, sizeof(int32_t) * (size_t)(n + 1), kind, st);
+        if (e == cudaSuccess) e = widen_offsets(off32, g->off, n + 1, sms, st);
     }
-    g->n_small = (int64_t)ls.size();
-    g->n_mid = (int64_t)lm.size();
-    g->n_big = (int64_t)lb.size();
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(g->adj, adj, sizeof(int32_t) * (size_t)nnz, kind, st);
+    // offsets check, degree classes, sort keys
+    if (e == cudaSuccess) e = degree_stats(n, nnz, g->off, d_stats, rank_keys(n, scratch), sms, st);
+    DegreeStats hs;
+    memset(&hs, 0, sizeof(hs));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(CBFS_E_CUDA);
+    if (hs.bad) return fail(CBFS_E_GRAPH);
+    dev_free(off32);
+    g->n_small = (int64_t)hs.n_small;
+    g->n_mid = (int64_t)hs.n_mid;
+    g->n_big = (int64_t)hs.n_big;
+    g->big_pieces = (int64_t)hs.big_pieces;
     const int64_t nlist = g->n_small + g->n_mid + g->n_big;
     rc = dev_alloc(&g->pl, nlist);
     if (rc) return fail(rc);
-    int sms = 0, occ = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    sms = std::max(1, sms);
     const void* kb[4] = {(const void*)k_phase_b<1>, (const void*)k_phase_b<2>, (const void*)k_phase_b<4>,
                          (const void*)k_phase_b<8>};
     for (int i = 0; i < 4; ++i) {
@@ -1584,82 +1667,61 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb[i], kThreads, 0);
         g->grid_p[i] = sms * std::max(1, std::min(occ, 8));
     }
+    // internal order: ranks by degree (cbfs_relabel.cu); the degree classes are rank ranges
+    e = rank_order_device(n, g->off, hs.maxdeg, scratch, g->perm, g->iperm_d, g->off_r, d_stats, sms, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || hs.order_bad) return fail(CBFS_E_CUDA);
     if (validate && n > 0) {
-        if (g->n_small) cudaMemcpyAsync(g->pl, ls.data(), sizeof(int32_t) * ls.size(), cudaMemcpyHostToDevice, st);
-        if (g->n_mid) cudaMemcpyAsync(g->pl + g->n_small, lm.data(), sizeof(int32_t) * lm.size(), cudaMemcpyHostToDevice, st);
-        if (g->n_big)
-            cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, lb.data(), sizeof(int32_t) * lb.size(), cudaMemcpyHostToDevice, st);
-        if (cudaMemsetAsync(g->status, 0, sizeof(int), st) != cudaSuccess) return fail(CBFS_E_CUDA);
-        k_validate<<<sms * 8, kThreads, 0, st>>>(n, g->off, g->adj, g->pl, g->n_small, g->pl + g->n_small, g->n_mid,
-                                                 g->pl + g->n_small + g->n_mid, g->n_big, g->status);
+        // every arc has its reverse, no self-loops or repeats; lists of the
+        // three degree classes are balanced separately (thread, warp, CTA per list)
+        e = cudaMemsetAsync(g->status, 0, sizeof(int), st);
+        if (e == cudaSuccess) {
+            k_validate<<<sms * 8, kThreads, 0, st>>>(n, g->off, g->adj, g->perm + g->n_big + g->n_mid, g->n_small,
+                                                     g->perm + g->n_big, g->n_mid, g->perm, g->n_big, g->status);
+            e = cudaGetLastError();
+        }
         int flag = 0;
-        if (cudaMemcpyAsync(&flag, g->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(CBFS_E_CUDA);
-        if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, g->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return fail(CBFS_E_CUDA);
         if (flag) return fail(CBFS_E_GRAPH);
     }
-    // internal order: ranks by degree, hub-first adjacency (cbfs_relabel.cu)
-    std::vector<int32_t> perm;
-    std::vector<int64_t> off_r;
-    rank_order(n, h_off.data(), perm, g->iperm, off_r);
-    int32_t* d_iperm = nullptr;
-    rc = dev_alloc(&g->off_r, n + 1);
-    if (!rc) rc = dev_alloc(&g->adj_r, nnz);
-    if (!rc) rc = dev_alloc(&g->perm, n);
-    if (!rc) rc = dev_alloc(&d_iperm, n);
-    if (rc) {
-        dev_free(d_iperm);
-        return fail(rc);
-    }
-    cudaError_t e = cudaSuccess;
-    if (n > 0) {
-        e = cudaMemcpyAsync(g->off_r, off_r.data(), sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(g->perm, perm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_iperm, g->iperm.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && nnz > 0)
-            e = relabel_adjacency(n, g->n_big, g->n_mid, g->n_small, g->perm, d_iperm, g->off, g->adj, g->off_r, g->adj_r,
-                                  sms, st);
-    } else {
-        e = cudaMemsetAsync(g->off_r, 0, sizeof(int64_t), st);
-    }
-    // pieces of the high-degree lists for the dense edge phase (ranks [0, n_big))
-    {
-        // piece-major order (every hub's first piece before any second piece):
-        // a later piece usually finds its hub already complete and skips
-        std::vector<uint64_t> pcs;
-        pcs.reserve((size_t)g->big_pieces);
-        for (int64_t k = 0; (int64_t)pcs.size() < g->big_pieces; ++k) {
-            for (int64_t r = 0; r < g->n_big; ++r) {
-                const int64_t dg = off_r[(size_t)r + 1] - off_r[(size_t)r];
-                if (k * kBigDeg < dg) pcs.push_back(((uint64_t)r << 32) | (uint64_t)k);
-                else break;  // ranks are sorted by degree: the rest are shorter
-            }
-        }
-        if (e == cudaSuccess && dev_alloc(&g->pull_pieces, (int64_t)pcs.size()) != CBFS_OK) e = cudaErrorMemoryAllocation;
-        if (e == cudaSuccess && !pcs.empty())
-            e = cudaMemcpyAsync(g->pull_pieces, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && (int64_t)pcs.size() != g->big_pieces) e = cudaErrorInvalidValue;
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // pcs dies with this scope
-    }
-    // pull lists in rank space: the degree classes are consecutive rank ranges
-    std::vector<int32_t> ranks((size_t)nlist);
-    for (int64_t i = 0; i < nlist; ++i) ranks[(size_t)i] = (int32_t)i;
-    // order inside pl: small | mid | big, as the traversal expects
-    if (e == cudaSuccess && g->n_small)
-        e = cudaMemcpyAsync(g->pl, ranks.data() + g->n_big + g->n_mid, sizeof(int32_t) * (size_t)g->n_small,
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && g->n_mid)
-        e = cudaMemcpyAsync(g->pl + g->n_small, ranks.data() + g->n_big, sizeof(int32_t) * (size_t)g->n_mid,
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && g->n_big)
-        e = cudaMemcpyAsync(g->pl + g->n_small + g->n_mid, ranks.data(), sizeof(int32_t) * (size_t)g->n_big,
-                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nnz > 0)
+        e = relabel_adjacency(n, g->n_big, g->n_mid, g->n_small, g->perm, g->iperm_d, g->off, g->adj, g->off_r, g->adj_r,
+                              sms, st);
+    if (e == cudaSuccess) e = class_lists(g->pl, g->n_small, g->n_mid, g->n_big, sms, st);
+    // pieces of the high-degree lists for the dense edge phase (ranks [0, n_big)),
+    // piece-major (every hub's first piece before any second piece): a later
+    // piece usually finds its hub already complete and skips
+    std::vector<int64_t> hub_off((size_t)g->n_big + 1, 0);
+    if (e == cudaSuccess && g->n_big > 0)
+        e = cudaMemcpyAsync(hub_off.data(), g->off_r, sizeof(int64_t) * hub_off.size(), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    g->iperm_d = d_iperm;
     if (e != cudaSuccess) return fail(CBFS_E_CUDA);
+    std::vector<uint64_t> pcs;
+    pcs.reserve((size_t)g->big_pieces);
+    static_assert(kBigDeg == kPullMid, "the push big list and the CTA pull class are the same vertices");
+    g->big_vertices = g->n_big;
+    for (int64_t k = 0; (int64_t)pcs.size() < g->big_pieces; ++k) {
+        bool any = false;
+        for (int64_t r = 0; r < g->n_big; ++r) {
+            const int64_t dg = hub_off[(size_t)r + 1] - hub_off[(size_t)r];
+            if (k * kBigDeg >= dg) break;  // ranks are sorted by degree: the rest are shorter
+            pcs.push_back(((uint64_t)r << 32) | (uint64_t)k);
+            any = true;
+        }
+        if (!any) break;
+    }
+    if ((int64_t)pcs.size() != g->big_pieces) return fail(CBFS_E_CUDA);
+    if (dev_alloc(&g->pull_pieces, (int64_t)pcs.size()) != CBFS_OK) return fail(CBFS_E_NOMEM);
+    if (!pcs.empty())
+        e = cudaMemcpyAsync(g->pull_pieces, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // pcs dies with this scope
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(CBFS_E_CUDA);
+    dev_free(scratch);
+    dev_free(d_stats);
     dev_free(g->adj);  // the caller's adjacency is no longer needed
-    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CBFS_E_CUDA);
-    if (cudaGetLastError() != cudaSuccess) return fail(CBFS_E_CUDA);
     *out = g;
     return CBFS_OK;
 }
@@ -1684,6 +1746,12 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->seeds);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     for (auto& ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+    dev_free(g->stage);
+    if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+    for (int b = 0; b < 2; ++b) {
+        if (g->ev_emit[b]) cudaEventDestroy(g->ev_emit[b]);
+        if (g->ev_copy[b]) cudaEventDestroy(g->ev_copy[b]);
+    }
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->cap_stream2) cudaStreamDestroy(g->cap_stream2);
     dev_free(g->round_dev);
@@ -1711,7 +1779,7 @@ int cbfs_run(cbfs_graph_t g, const int32_t* host_sources, int k, int d, uint8_t*
     cbfs_tune_t t;
     memset(&t, 0, sizeof(t));
     t.slots = 1;
-    return run_clusters(g, host_sources, coff, 1, d, dist, masks, &t, (cudaStream_t)stream);
+    return run_clusters(g, host_sources, coff, 1, d, dist, masks, nullptr, &t, (cudaStream_t)stream);
 }
 
 int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const int32_t* host_cluster_off, int C,
@@ -1719,7 +1787,18 @@ int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const i
     if (!g || C < 0 || !host_cluster_off) return CBFS_E_INVALID;
     if (C == 0) return CBFS_OK;
     if (!host_sources_concat || !dist || (d > 0 && !masks)) return CBFS_E_INVALID;
-    return run_clusters(g, host_sources_concat, host_cluster_off, C, d, dist, masks, tune, (cudaStream_t)stream);
+    return run_clusters(g, host_sources_concat, host_cluster_off, C, d, dist, masks, nullptr, tune,
+                        (cudaStream_t)stream);
+}
+
+int cbfs_run_batched_labels(cbfs_graph_t g, const int32_t* host_sources_concat, const int32_t* host_cluster_off,
+                            int C, int d, uint8_t* dist, uint64_t* masks, cbfs_labels_t labels,
+                            const cbfs_tune_t* tune, void* stream) {
+    if (!g || C < 0 || !host_cluster_off || !labels) return CBFS_E_INVALID;
+    if (C == 0) return CBFS_OK;
+    if (!host_sources_concat || (!dist && masks) || (dist && d > 0 && !masks)) return CBFS_E_INVALID;
+    return run_clusters(g, host_sources_concat, host_cluster_off, C, d, dist, masks, labels, tune,
+                        (cudaStream_t)stream);
 }
 
 int cbfs_profile(cbfs_graph_t g, int enable, cbfs_kernel_times_t* host_out) {

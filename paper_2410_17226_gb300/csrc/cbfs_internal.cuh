@@ -136,16 +136,45 @@ __global__ void k_phase_b(Wave w, int round);
 template <int P>
 __global__ void k_emit(Wave w, const int32_t* iperm);
 
-// Internal vertex order (cbfs_relabel.cu): ranks by degree, highest first,
-// ties to the smaller id; perm[rank] = id, iperm[id] = rank, off_r = offsets
-// of the relabelled CSR.
-void rank_order(int64_t n, const int64_t* h_off, std::vector<int32_t>& perm, std::vector<int32_t>& iperm,
-                std::vector<int64_t>& off_r);
+// Internal vertex order (cbfs_relabel.cu), computed on the device: ranks by
+// degree, highest first, ties to the smaller id; perm[rank] = id,
+// iperm[id] = rank, off_r = offsets of the relabelled CSR.
+struct DegreeStats {
+    unsigned long long n_small, n_mid, n_big;  // non-isolated vertices by degree class (kPullSmall, kPullMid)
+    unsigned long long big_pieces;             // kBigDeg-arc pieces of the lists longer than kBigDeg
+    unsigned long long maxdeg;
+    unsigned long long bad;                    // offsets not starting at 0, not ending at nnz, or decreasing
+    unsigned long long order_bad;              // the rank order failed its check (never expected)
+};
+cudaError_t widen_offsets(const int32_t* in, int64_t* out, int64_t count, int sms, cudaStream_t st);
+int64_t rank_scratch_words(int64_t n);
+uint32_t* rank_keys(int64_t n, int64_t* scratch);
+// Checks the offsets, fills st_dev and writes the sort keys into the scratch.
+cudaError_t degree_stats(int64_t n, int64_t nnz, const int64_t* off, DegreeStats* st_dev, uint32_t* keys, int sms,
+                         cudaStream_t st);
+// Also checks its result into st_dev->order_bad.
+cudaError_t rank_order_device(int64_t n, const int64_t* off, uint64_t maxdeg, int64_t* scratch, int32_t* perm,
+                              int32_t* iperm, int64_t* off_r, DegreeStats* st_dev, int sms, cudaStream_t st);
+// Exclusive scan of count int64 values into out[0..count] (out[count] = total);
+// in == out is allowed.  sums: tile sums, (count + 4095) / 4096 entries.
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, int64_t* sums, cudaStream_t st);
+// Pull lists in rank space: small | mid | big.
+cudaError_t class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big, int sms, cudaStream_t st);
+// Seeds hold callers' ids in their low 32 bits: rewrite them as ranks.
+cudaError_t map_seeds(uint64_t* seeds, int64_t count, const int32_t* iperm, cudaStream_t st);
 // Writes the relabelled adjacency (ranks, hubs first) of the ranks
 // [0, n_big) (degree > kPullMid), then n_mid, then n_small vertices.
 cudaError_t relabel_adjacency(int64_t n, int64_t n_big, int64_t n_mid, int64_t n_small, const int32_t* d_perm,
                               const int32_t* d_iperm, const int64_t* d_off, const int32_t* d_adj, const int64_t* d_off_r,
                               int32_t* d_adj_r, int sms, cudaStream_t st);
+
+// Label store (cbfs_labels.cu) fed by a batched run: reserve C rows' worth of
+// clusters at the store's count (uploads their ALL words), write nc clusters
+// of cluster-major outputs at position pos, or undo a reservation.
+int labels_reserve(cbfs_labels_s* L, int64_t n, int d, const int32_t* coff, int C, int* base);
+cudaError_t labels_write(cbfs_labels_s* L, const uint8_t* dist, const uint64_t* masks, int nc, int pos,
+                         cudaStream_t st);
+void labels_rollback(cbfs_labels_s* L, int base);
 
 // Launches phase A (which = 0), phase B (1) of one round, or the emit
 // kernel (2) for w.P (1, 2, 4 or 8).

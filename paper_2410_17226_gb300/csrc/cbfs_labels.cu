@@ -155,6 +155,37 @@ __global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int cap,
 
 }  // namespace
 
+namespace cbfs {
+
+int labels_reserve(cbfs_labels_s* L, int64_t n, int d, const int32_t* coff, int C, int* base) {
+    if (L->n != n || L->d != d || C < 0) return CBFS_E_INVALID;
+    if (L->count + C > L->cap) return CBFS_E_NOMEM;
+    std::vector<uint64_t> alls((size_t)std::max(C, 1));
+    for (int c = 0; c < C; ++c) {
+        const int k = coff[c + 1] - coff[c];
+        if (k < 1 || k > 64) return CBFS_E_INVALID;
+        alls[c] = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
+    }
+    cudaSetDevice(L->device);
+    if (C > 0 && cudaMemcpy(L->alls + L->count, alls.data(), sizeof(uint64_t) * C, cudaMemcpyHostToDevice) != cudaSuccess)
+        return CBFS_E_CUDA;
+    *base = L->count;
+    L->count += C;
+    return CBFS_OK;
+}
+
+void labels_rollback(cbfs_labels_s* L, int base) { L->count = base; }
+
+cudaError_t labels_write(cbfs_labels_s* L, const uint8_t* dist, const uint64_t* masks, int C, int pos,
+                         cudaStream_t st) {
+    if (L->n == 0 || C == 0) return cudaSuccess;
+    dim3 grid((unsigned)((L->n + kTV - 1) / kTV), (unsigned)((C + kTC - 1) / kTC));
+    k_labels_append<<<grid, 256, 0, st>>>(L->n, L->d, C, pos, L->cap, L->P, L->stride, dist, masks, L->rows);
+    return cudaGetLastError();
+}
+
+}  // namespace cbfs
+
 extern "C" {
 
 int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes, cbfs_labels_t* out) {

@@ -117,25 +117,356 @@ __global__ void __launch_bounds__(kThreads) k_relabel_big(int64_t r0, int64_t r1
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------- rank order
+//
+// Ranks are produced on the device: a stable LSD radix sort of the key
+// 0xFFFFFFFF - deg(v) over the ids 0..n-1 (8-bit digits, only as many passes
+// as the largest degree has bits).  Ascending keys = descending degrees, and
+// stability keeps ascending ids within a degree.
+
+constexpr int kSortItems = 16;                    // items per thread per tile
+constexpr int kSortTile = kThreads * kSortItems;  // 4096 items per CTA
+
+__global__ void k_widen_off(const int32_t* in, int64_t* out, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Offsets check, degree statistics and the sort keys.
+__global__ void __launch_bounds__(kThreads) k_degree_stats(int64_t n, int64_t nnz, const int64_t* off, DegreeStats* st,
+                                                           uint32_t* keys) {
+    unsigned long long cls[4] = {0, 0, 0, 0};  // small, mid, big (> kPullMid), pieces of lists > kBigDeg
+    unsigned long long mx = 0;
+    int bad = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (off[0] != 0 || off[n] != nnz)) bad = 1;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t dg = off[v + 1] - off[v];
+        if (dg < 0 || dg > 0x7fffffffLL) {
+            bad = 1;
+            keys[v] = 0;
+            continue;
+        }
+        keys[v] = 0xFFFFFFFFu - (uint32_t)dg;
+        mx = dg > (int64_t)mx ? (unsigned long long)dg : mx;
+        if (dg == 0) continue;
+        if (dg <= kPullSmall) cls[0]++;
+        else if (dg <= kPullMid) cls[1]++;
+        else cls[2]++;
+        if (dg > kBigDeg) cls[3] += (unsigned long long)((dg + kBigDeg - 1) / kBigDeg);
+    }
+    __shared__ unsigned long long red[kWarps][5];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (bad) sbad = 1;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) cls[i] = warp_sum_u64(cls[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if (lane == 0) {
+        for (int i = 0; i < 4; ++i) red[wp][i] = cls[i];
+        red[wp][4] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t[5] = {0, 0, 0, 0, 0};
+        for (int k = 0; k < kWarps; ++k) {
+            for (int i = 0; i < 4; ++i) t[i] += red[k][i];
+            t[4] = red[k][4] > t[4] ? red[k][4] : t[4];
+        }
+        atomicAdd(&st->n_small, t[0]);
+        atomicAdd(&st->n_mid, t[1]);
+        atomicAdd(&st->n_big, t[2]);
+        atomicAdd(&st->big_pieces, t[3]);
+        atomicMax(&st->maxdeg, t[4]);
+        if (sbad) atomicExch(&st->bad, 1ull);
+    }
+}
+
+// Digit counts of one tile, stored digit-major: hist[digit * ntiles + tile].
+__global__ void __launch_bounds__(kThreads) k_sort_hist(const uint32_t* keys, int64_t n, int shift, int64_t* hist,
+                                                        int64_t ntiles) {
+    __shared__ unsigned int cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * kThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter of one tile: item order within a digit is kept by ranking
+// the tile in 16 rounds of 256 consecutive items (warp match, then per-warp
+// digit counts in shared memory, then a running count per digit).
+__global__ void __launch_bounds__(kThreads) k_sort_scatter(const uint32_t* keys_in, const int32_t* vals_in, int64_t n,
+                                                           int shift, const int64_t* start, int64_t ntiles,
+                                                           uint32_t* keys_out, int32_t* vals_out) {
+    __shared__ unsigned int wcnt[kWarps][256];
+    __shared__ unsigned int run[256];
+    __shared__ int64_t gbase[256];
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    run[t] = 0;
+    gbase[t] = start[(int64_t)t * ntiles + blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) wcnt[k][t] = 0;
+    __syncthreads();
+    const unsigned int lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+    for (int i = 0; i < kSortItems; ++i) {
+        const int64_t idx = base + i * kThreads + t;
+        const bool valid = idx < n;
+        const uint32_t key = valid ? keys_in[idx] : 0u;
+        const int32_t val = valid ? (vals_in ? vals_in[idx] : (int32_t)idx) : 0;
+        const unsigned int dg = valid ? ((key >> shift) & 255u) : 256u;
+        const unsigned int peers = __match_any_sync(0xffffffffu, dg);
+        const unsigned int wr = __popc(peers & lt);
+        if (valid && wr == 0) wcnt[wp][dg] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            unsigned int pos = run[dg] + wr;
+            for (int k = 0; k < wp; ++k) pos += wcnt[k][dg];
+            const int64_t at = gbase[dg] + pos;
+            if (at < n) {  // always true for a consistent histogram
+                keys_out[at] = key;
+                vals_out[at] = val;
+            }
+        }
+        __syncthreads();
+        unsigned int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) {
+            sum += wcnt[k][t];
+            wcnt[k][t] = 0;
+        }
+        run[t] += sum;
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of int64 values in tiles of kSortTile: per-tile sums, a
+// one-CTA scan of the sums, then per-tile prefixes.  out[count] = total.
+__device__ __forceinline__ int64_t block_exclusive_i64(int64_t x, int64_t* total) {
+    __shared__ int64_t ws[kWarps];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int64_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[wp] = inc;
+    __syncthreads();
+    int64_t before = 0, all = 0;
+    for (int k = 0; k < kWarps; ++k) {
+        if (k < wp) before += ws[k];
+        all += ws[k];
+    }
+    __syncthreads();
+    *total = all;
+    return before + inc - x;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const int64_t* in, int64_t count, int64_t* sums) {
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)threadIdx.x * kSortItems;
+    int64_t s = 0;
+    for (int i = 0; i < kSortItems; ++i)
+        if (base + i < count) s += in[base + i];
+    int64_t total;
+    block_exclusive_i64(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_sums(int64_t* sums, int64_t ntiles) {
+    int64_t carry = 0;
+    for (int64_t b = 0; b < ntiles; b += kThreads) {
+        const int64_t i = b + threadIdx.x;
+        const int64_t x = i < ntiles ? sums[i] : 0;
+        int64_t total;
+        const int64_t ex = block_exclusive_i64(x, &total);
+        if (i < ntiles) sums[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_apply(const int64_t* in, int64_t count, const int64_t* sums,
+                                                         int64_t* out) {
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)threadIdx.x * kSortItems;
+    int64_t v[kSortItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        v[i] = base + i < count ? in[base + i] : 0;
+        s += v[i];
+    }
+    int64_t total;
+    int64_t run = sums[blockIdx.x] + block_exclusive_i64(s, &total);
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+        if (base + i < count) out[base + i] = run;
+        run += v[i];
+        if (base + i == count - 1) out[count] = run;
+    }
+}
+
+__global__ void k_rank_finish(int64_t n, const int32_t* perm, const int64_t* off, int32_t* iperm, int64_t* deg_r) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = perm[r];
+        iperm[v] = (int32_t)r;
+        deg_r[r] = off[v + 1] - off[v];
+    }
+}
+
+// The relabel kernels size their buffers by degree class, so the order is
+// checked before they run: perm and iperm are inverse permutations and the
+// degrees never increase along the ranks.
+__global__ void k_check_rank(int64_t n, const int32_t* perm, const int32_t* iperm, const int64_t* deg_r,
+                             DegreeStats* st) {
+    bool bad = false;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = iperm[v];
+        if (r < 0 || (int64_t)r >= n || perm[r] != (int32_t)v) bad = true;
+        if (v + 1 < n && deg_r[v] < deg_r[v + 1]) bad = true;
+    }
+    if (bad) atomicExch(&st->order_bad, 1ull);
+}
+
+// Pull lists in rank space, in the order small | mid | big: the degree
+// classes are consecutive rank ranges (big first).
+__global__ void k_class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big) {
+    const int64_t total = n_small + n_mid + n_big;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r;
+        if (i < n_small) r = n_big + n_mid + i;
+        else if (i < n_small + n_mid) r = n_big + (i - n_small);
+        else r = i - n_small - n_mid;
+        pl[i] = (int32_t)r;
+    }
+}
+
+__global__ void k_map_seeds(uint64_t* seeds, int64_t count, const int32_t* iperm) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = seeds[i];
+        seeds[i] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)iperm[(uint32_t)e];
+    }
+}
+
+int64_t tiles_of(int64_t count) { return (count + kSortTile - 1) / kSortTile; }
+
+}  // namespace
+
 namespace cbfs {
 
-void rank_order(int64_t n, const int64_t* h_off, std::vector<int32_t>& perm, std::vector<int32_t>& iperm,
-                std::vector<int64_t>& off_r) {
-    int64_t maxdeg = 0;
-    for (int64_t v = 0; v < n; ++v) maxdeg = std::max(maxdeg, h_off[v + 1] - h_off[v]);
-    // counting sort by degree, descending; ascending ids within a degree
-    std::vector<int64_t> start((size_t)maxdeg + 2, 0);
-    for (int64_t v = 0; v < n; ++v) start[(size_t)(maxdeg - (h_off[v + 1] - h_off[v])) + 1]++;
-    for (size_t b = 1; b < start.size(); ++b) start[b] += start[b - 1];
-    perm.assign((size_t)n, 0);
-    iperm.assign((size_t)n, 0);
-    for (int64_t v = 0; v < n; ++v) {
-        const int64_t r = start[(size_t)(maxdeg - (h_off[v + 1] - h_off[v]))]++;
-        perm[(size_t)r] = (int32_t)v;
-        iperm[(size_t)v] = (int32_t)r;
+cudaError_t widen_offsets(const int32_t* in, int64_t* out, int64_t count, int sms, cudaStream_t st) {
+    if (count > 0) k_widen_off<<<sms * 8, kThreads, 0, st>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+cudaError_t degree_stats(int64_t n, int64_t nnz, const int64_t* off, DegreeStats* st_dev, uint32_t* keys, int sms,
+                         cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(st_dev, 0, sizeof(DegreeStats), st);
+    if (e != cudaSuccess) return e;
+    k_degree_stats<<<sms * 8, kThreads, 0, st>>>(n, nnz, off, st_dev, keys);
+    return cudaGetLastError();
+}
+
+// Scratch of the rank order, in int64 words:
+//   keys | keys2 | vals_a | vals_b (n 32-bit entries each) | hist (256 per tile, + 1)
+//   | tile sums | deg_r (n)
+struct RankScratch {
+    uint32_t *keys, *keys2;
+    int32_t *vals_a, *vals_b;
+    int64_t *hist, *sums, *deg_r;
+    int64_t words;
+};
+
+static RankScratch rank_layout(int64_t n, int64_t* base) {
+    const int64_t half = n / 2 + 1;
+    const int64_t nh = 256 * tiles_of(n);
+    const int64_t o_hist = 4 * half, o_sums = o_hist + nh + 1;
+    const int64_t o_deg = o_sums + tiles_of(nh + 1) + tiles_of(n) + 1;
+    RankScratch r;
+    r.words = o_deg + n + 1;
+    r.keys = base ? (uint32_t*)base : nullptr;
+    r.keys2 = base ? (uint32_t*)(base + half) : nullptr;
+    r.vals_a = base ? (int32_t*)(base + 2 * half) : nullptr;
+    r.vals_b = base ? (int32_t*)(base + 3 * half) : nullptr;
+    r.hist = base ? base + o_hist : nullptr;
+    r.sums = base ? base + o_sums : nullptr;
+    r.deg_r = base ? base + o_deg : nullptr;
+    return r;
+}
+
+int64_t rank_scratch_words(int64_t n) { return rank_layout(n, nullptr).words; }
+
+uint32_t* rank_keys(int64_t n, int64_t* scratch) { return rank_layout(n, scratch).keys; }
+
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, int64_t* sums, cudaStream_t st) {
+    if (count <= 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+    const int64_t tiles = tiles_of(count);
+    k_scan_reduce<<<(unsigned)tiles, kThreads, 0, st>>>(in, count, sums);
+    k_scan_sums<<<1, kThreads, 0, st>>>(sums, tiles);
+    k_scan_apply<<<(unsigned)tiles, kThreads, 0, st>>>(in, count, sums, out);
+    return cudaGetLastError();
+}
+
+cudaError_t rank_order_device(int64_t n, const int64_t* off, uint64_t maxdeg, int64_t* scratch, int32_t* perm,
+                              int32_t* iperm, int64_t* off_r, DegreeStats* st_dev, int sms, cudaStream_t st) {
+    if (n == 0) return cudaMemsetAsync(off_r, 0, sizeof(int64_t), st);
+    const RankScratch r = rank_layout(n, scratch);
+    const int64_t tiles = tiles_of(n);
+    const int64_t nh = 256 * tiles;
+    int passes = 1;  // at least one pass: it also writes the identity values
+    while (passes < 4 && (maxdeg >> (8 * passes)) != 0) passes++;
+    uint32_t* kin = r.keys;
+    uint32_t* kout = r.keys2;
+    const int32_t* vin = nullptr;  // the ids themselves on the first pass
+    int32_t* vout = r.vals_a;
+    for (int p = 0; p < passes; ++p) {
+        k_sort_hist<<<(unsigned)tiles, kThreads, 0, st>>>(kin, n, 8 * p, r.hist, tiles);
+        // in place: every tile of the scan rewrites only the entries it read
+        cudaError_t e = exclusive_scan_i64(r.hist, nh, r.hist, r.sums, st);
+        if (e != cudaSuccess) return e;
+        k_sort_scatter<<<(unsigned)tiles, kThreads, 0, st>>>(kin, vin, n, 8 * p, r.hist, tiles, kout, vout);
+        std::swap(kin, kout);
+        vin = vout;
+        vout = (vout == r.vals_a) ? r.vals_b : r.vals_a;
     }
-    off_r.assign((size_t)n + 1, 0);
-    for (int64_t r = 0; r < n; ++r) off_r[(size_t)r + 1] = off_r[(size_t)r] + (h_off[perm[r] + 1] - h_off[perm[r]]);
+    cudaError_t e = cudaMemcpyAsync(perm, vin, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(iperm, 0xFF, sizeof(int32_t) * (size_t)n, st);
+    if (e != cudaSuccess) return e;
+    k_rank_finish<<<sms * 8, kThreads, 0, st>>>(n, perm, off, iperm, r.deg_r);
+    k_check_rank<<<sms * 8, kThreads, 0, st>>>(n, perm, iperm, r.deg_r, st_dev);
+    e = exclusive_scan_i64(r.deg_r, n, off_r, r.sums, st);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big, int sms, cudaStream_t st) {
+    if (n_small + n_mid + n_big > 0) k_class_lists<<<sms * 8, kThreads, 0, st>>>(pl, n_small, n_mid, n_big);
+    return cudaGetLastError();
+}
+
+cudaError_t map_seeds(uint64_t* seeds, int64_t count, const int32_t* iperm, cudaStream_t st) {
+    if (count > 0)
+        k_map_seeds<<<(unsigned)std::min<int64_t>((count + kThreads - 1) / kThreads, 1024), kThreads, 0, st>>>(seeds, count,
+                                                                                                           iperm);
+    return cudaGetLastError();
 }
 
 cudaError_t relabel_adjacency(int64_t n, int64_t n_big, int64_t n_mid, int64_t n_small, const int32_t* d_perm,
