@@ -972,13 +972,12 @@ struct cbfs_graph_s {
     std::vector<uint64_t> seen;      // call shapes run once (host-driven) and not yet captured
     int* wave_flags = nullptr;       // host-driven: waves that needed more rounds than enqueued
     int64_t wave_flags_cap = 0;
-    // staged outputs (host destinations or a label store): two wave buffers,
-    // copied out on copy_stream while the next wave traverses
+    // staged outputs (host destinations, or labels without outputs): a ring
+    // of wave buffers, copied out on copy_stream while later waves traverse
     uint8_t* stage = nullptr;
     int64_t stage_cap = 0;
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_emit[2] = {nullptr, nullptr};
-    cudaEvent_t ev_copy[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_emit, ev_copy;  // one pair per ring slot
 };
 
 namespace {
@@ -1288,29 +1287,54 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     const int grid = g->grid_p[P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3];
     const int nwaves = (C + P - 1) / P;
     const int64_t total_src = coff[C];
-    // staged mode: every wave emits into one of two device buffers of P
-    // clusters, [dist P x n | masks P x d x n], then copies out / appends
-    const bool staged = L || (dist && is_host_pointer(dist)) || (masks && is_host_pointer(masks));
-    const int64_t stage_dist_bytes = ((int64_t)P * g->n + 255) / 256 * 256;
-    const int64_t stage_slot = stage_dist_bytes + (int64_t)P * d * g->n * 8;
+    const int64_t n = g->n;
+    // Where each wave's outputs go.  Device outputs: straight into dist/masks.
+    // Host outputs (or labels without outputs): a ring of G wave buffers,
+    // [dist G x P x n | masks G x P x d x n] so consecutive slots form one
+    // cluster-major array; each wave is copied out on copy_stream while later
+    // waves traverse.  Labels are written per group of waves (about
+    // kLabelGroup clusters) from wherever the outputs are: the row store is
+    // vertex-major, and a wider group writes longer runs of each row.
+    constexpr int kLabelGroup = 32;
+    constexpr int64_t kStageBudget = (int64_t)3 << 30;
+    const bool host_out = (dist && is_host_pointer(dist)) || (masks && is_host_pointer(masks));
+    const bool staged = host_out || (L && !dist);
+    const int64_t wave_dist = (int64_t)P * n;       // bytes
+    const int64_t wave_masks = (int64_t)P * d * n;  // words
+    int G = 2;
+    if (staged && L) {
+        G = std::max(2, kLabelGroup / P);
+        const int64_t fit = kStageBudget / std::max<int64_t>(1, wave_dist + 8 * wave_masks);
+        G = (int)std::max<int64_t>(2, std::min<int64_t>(G, fit));
+    }
+    const int LG = L ? (staged ? G : std::max(1, kLabelGroup / P)) : 0;  // waves per label write
+    const int64_t stage_dist_bytes = (G * wave_dist + 255) / 256 * 256;
     if (staged) {
-        rc = ensure_dev(&g->stage, &g->stage_cap, 2 * stage_slot);
+        rc = ensure_dev(&g->stage, &g->stage_cap, stage_dist_bytes + 8 * G * wave_masks);
         if (rc) return rc;
-        if (!g->copy_stream) {
-            CK(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
-            for (int b = 0; b < 2; ++b) {
-                CK(cudaEventCreateWithFlags(&g->ev_emit[b], cudaEventDisableTiming));
-                CK(cudaEventCreateWithFlags(&g->ev_copy[b], cudaEventDisableTiming));
-            }
+        if (!g->copy_stream) CK(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+        while ((int)g->ev_emit.size() < G) {
+            cudaEvent_t a = nullptr, b = nullptr;
+            CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+            g->ev_emit.push_back(a);
+            CK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+            g->ev_copy.push_back(b);
         }
     }
+    uint64_t* stage_masks = staged ? reinterpret_cast<uint64_t*>(g->stage + stage_dist_bytes) : nullptr;
+    auto wave_dist_at = [&](int wv) -> uint8_t* {
+        return staged ? g->stage + (size_t)(wv % G) * (size_t)wave_dist : dist + (size_t)wv * (size_t)wave_dist;
+    };
+    auto wave_masks_at = [&](int wv) -> uint64_t* {
+        if (!d) return nullptr;
+        return staged ? stage_masks + (size_t)(wv % G) * (size_t)wave_masks : masks + (size_t)wv * (size_t)wave_masks;
+    };
     rc = ensure_dev(&g->slots, &g->slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_pinned(&g->h_slots, &g->h_slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_dev(&g->seeds, &g->seeds_cap, total_src);
     if (!rc) rc = ensure_pinned(&g->h_seeds, &g->h_seeds_cap, total_src);
     if (rc) return rc;
     // slot tables and seeds of every wave, staged once
-    const int64_t n = g->n;
     std::vector<int64_t> wave_seed_off(nwaves + 1, 0);
     int64_t ns = 0;
     for (int wv = 0; wv < nwaves; ++wv) {
@@ -1321,15 +1345,8 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
             memset(&sd, 0, sizeof(sd));
             if (c < C) {
                 const int k = coff[c + 1] - coff[c];
-                if (staged) {
-                    uint8_t* base = g->stage + (size_t)(wv % 2) * (size_t)stage_slot;
-                    sd.dist = base + (size_t)s * (size_t)n;
-                    sd.masks = d ? reinterpret_cast<uint64_t*>(base + stage_dist_bytes) + (size_t)s * (size_t)d * (size_t)n
-                                 : nullptr;
-                } else {
-                    sd.dist = dist + (size_t)c * (size_t)n;
-                    sd.masks = d ? masks + (size_t)c * (size_t)d * (size_t)n : nullptr;
-                }
+                sd.dist = wave_dist_at(wv) + (size_t)s * (size_t)n;
+                sd.masks = d ? wave_masks_at(wv) + (size_t)s * (size_t)d * (size_t)n : nullptr;
                 sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
                 sd.cluster = c;
                 for (int j = 0; j < k; ++j)
@@ -1389,7 +1406,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     // Graph mode: a call shape seen before runs as one cached CUDA graph whose
     // rounds loop on the device; a first sighting runs host-driven below and
     // is remembered, so one-off calls (a fresh handle) pay no capture.
-    if (!g->timing && !(tune && tune->host_loop) && !staged) {
+    if (!g->timing && !(tune && tune->host_loop) && !staged && !L) {
         if (!g->round_dev) {
             rc = dev_alloc(&g->round_dev, 1);
             if (!rc) rc = dev_alloc(&g->iters, 1);
@@ -1458,7 +1475,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     rc = ensure_dev(&g->wave_flags, &g->wave_flags_cap, nwaves);
     if (rc) return rc;
     CK(cudaMemsetAsync(g->wave_flags, 0, sizeof(int) * (size_t)nwaves, st));
-    auto run_wave = [&](int wv, int bound, int* rounds_out) -> int {
+    auto run_wave = [&](int wv, int bound, bool rerun, int* rounds_out) -> int {
         const int c0 = wv * P;
         w.nslots = std::min(P, C - c0);
         w.slots = g->slots + (size_t)wv * P;
@@ -1508,27 +1525,31 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                 return CBFS_E_DEPTH;
             }
         }
-        const int b = wv % 2;
-        if (staged) CK(cudaStreamWaitEvent(st, g->ev_copy[b], 0));  // buffer b copied out by wave wv - 2
+        const int b = wv % G;
+        if (host_out) CK(cudaStreamWaitEvent(st, g->ev_copy[b], 0));  // ring slot b copied out (wave wv - G)
         ev = prof_begin(g, 0, st);
         CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
         prof_end(g, ev, st);
-        if (staged) {
-            const uint8_t* sdist = g->stage + (size_t)b * (size_t)stage_slot;
-            const uint64_t* smasks = reinterpret_cast<const uint64_t*>(sdist + stage_dist_bytes);
-            if (dist || masks) {
-                CK(cudaEventRecord(g->ev_emit[b], st));
-                CK(cudaStreamWaitEvent(g->copy_stream, g->ev_emit[b], 0));
-                if (dist)
-                    CK(cudaMemcpyAsync(dist + (size_t)c0 * (size_t)n, sdist, (size_t)w.nslots * (size_t)n, cudaMemcpyDefault,
-                                       g->copy_stream));
-                if (masks && d)
-                    CK(cudaMemcpyAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, smasks,
-                                       sizeof(uint64_t) * (size_t)w.nslots * (size_t)d * (size_t)n, cudaMemcpyDefault,
-                                       g->copy_stream));
-                CK(cudaEventRecord(g->ev_copy[b], g->copy_stream));
+        if (host_out) {
+            CK(cudaEventRecord(g->ev_emit[b], st));
+            CK(cudaStreamWaitEvent(g->copy_stream, g->ev_emit[b], 0));
+            if (dist)
+                CK(cudaMemcpyAsync(dist + (size_t)c0 * (size_t)n, wave_dist_at(wv), (size_t)w.nslots * (size_t)n,
+                                   cudaMemcpyDefault, g->copy_stream));
+            if (masks && d)
+                CK(cudaMemcpyAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, wave_masks_at(wv),
+                                   sizeof(uint64_t) * (size_t)w.nslots * (size_t)d * (size_t)n, cudaMemcpyDefault,
+                                   g->copy_stream));
+            CK(cudaEventRecord(g->ev_copy[b], g->copy_stream));
+        }
+        if (L) {
+            if (rerun) {
+                CK(labels_write(L, wave_dist_at(wv), wave_masks_at(wv), w.nslots, lbase + c0, st));
+            } else if ((wv + 1) % LG == 0 || wv == nwaves - 1) {
+                const int g0 = wv / LG * LG;  // first wave of the group (ring slot 0 when staged)
+                const int nc = std::min(C, (wv + 1) * P) - g0 * P;
+                CK(labels_write(L, wave_dist_at(g0), wave_masks_at(g0), nc, lbase + g0 * P, st));
             }
-            if (L) CK(labels_write(L, sdist, smasks, w.nslots, lbase + c0, st));
         }
         ev = prof_begin(g, 0, st);
         k_check_sources<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt, bound, g->wave_flags + wv);
@@ -1542,7 +1563,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     for (int wv = 0; wv < nwaves; ++wv) {
         const int bound = est > 0 ? std::min(est + 2, kMaxRounds - 1) : 0;
         int used = 0;
-        rc = run_wave(wv, bound, &used);
+        rc = run_wave(wv, bound, false, &used);
         if (rc) return rc;
         if (bound == 0) est = used;
         else any_optimistic = true;
@@ -1554,14 +1575,12 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         for (int wv = 0; wv < nwaves; ++wv) {
             if (!flags[wv]) continue;
             int used = 0;
-            rc = run_wave(wv, 0, &used);
+            rc = run_wave(wv, 0, true, &used);
             if (rc) return rc;
         }
     }
-    if (staged && (dist || masks)) {
-        CK(cudaStreamWaitEvent(st, g->ev_copy[0], 0));
-        CK(cudaStreamWaitEvent(st, g->ev_copy[1], 0));
-    }
+    if (host_out)
+        for (int b = 0; b < G; ++b) CK(cudaStreamWaitEvent(st, g->ev_copy[b], 0));
     int status = 0;
     CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1748,10 +1767,8 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     for (auto& ge : g->graphs) cudaGraphExecDestroy(ge.exec);
     dev_free(g->stage);
     if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
-    for (int b = 0; b < 2; ++b) {
-        if (g->ev_emit[b]) cudaEventDestroy(g->ev_emit[b]);
-        if (g->ev_copy[b]) cudaEventDestroy(g->ev_copy[b]);
-    }
+    for (cudaEvent_t e : g->ev_emit) cudaEventDestroy(e);
+    for (cudaEvent_t e : g->ev_copy) cudaEventDestroy(e);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->cap_stream2) cudaStreamDestroy(g->cap_stream2);
     dev_free(g->round_dev);

@@ -75,6 +75,25 @@ __global__ void __launch_bounds__(256) k_labels_append(int64_t n, int d, int C, 
     }
 }
 
+// Rows of the few (<= 8) clusters of one traversal wave at position pos, from
+// their cluster-major outputs: thread per (vertex, cluster), cluster fastest,
+// so the lanes of a warp fill whole runs of each row while reading nc
+// coalesced streams.  (The tile transpose above would leave most of its
+// 32-cluster tile idle.)
+__global__ void __launch_bounds__(256) k_labels_wave(int64_t n, int d, int nc, int pos, int cap, int64_t P,
+                                                     int64_t stride, const uint8_t* dist, const uint64_t* masks,
+                                                     uint8_t* rows) {
+    const int64_t total = n * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = t / nc;
+        const int c = (int)(t - v * nc);
+        uint8_t* row = rows + v * stride;
+        row[pos + c] = dist[(size_t)c * (size_t)n + v];
+        uint64_t* m = reinterpret_cast<uint64_t*>(row + P) + pos + c;
+        for (int s = 0; s < d; ++s) m[(size_t)s * cap] = masks[((size_t)c * (size_t)d + s) * (size_t)n + v];
+    }
+}
+
 // Smallest t = i + j with Su[i] & Sv[j] != 0, or -1.
 template <int D>
 __device__ __forceinline__ int best_offset_fixed(const uint64_t* su, const uint64_t* sv) {
@@ -179,8 +198,16 @@ void labels_rollback(cbfs_labels_s* L, int base) { L->count = base; }
 cudaError_t labels_write(cbfs_labels_s* L, const uint8_t* dist, const uint64_t* masks, int C, int pos,
                          cudaStream_t st) {
     if (L->n == 0 || C == 0) return cudaSuccess;
-    dim3 grid((unsigned)((L->n + kTV - 1) / kTV), (unsigned)((C + kTC - 1) / kTC));
-    k_labels_append<<<grid, 256, 0, st>>>(L->n, L->d, C, pos, L->cap, L->P, L->stride, dist, masks, L->rows);
+    if (C <= 8) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, L->device);
+        const int64_t blocks = std::min<int64_t>((L->n * C + 255) / 256, (int64_t)std::max(sms, 1) * 8);
+        k_labels_wave<<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, C, pos, L->cap, L->P, L->stride, dist, masks,
+                                                        L->rows);
+    } else {
+        dim3 grid((unsigned)((L->n + kTV - 1) / kTV), (unsigned)((C + kTC - 1) / kTC));
+        k_labels_append<<<grid, 256, 0, st>>>(L->n, L->d, C, pos, L->cap, L->P, L->stride, dist, masks, L->rows);
+    }
     return cudaGetLastError();
 }
 

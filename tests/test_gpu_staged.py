@@ -176,3 +176,32 @@ def test_degree_order_on_skewed_graphs(cb, shape):
     for c, S in enumerate(clusters):
         od, om = O.cbfs_definition(off, adj, S, d)
         assert (dist[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(masks[c]) == om).all()
+
+
+@pytest.mark.parametrize("slots", [1, 2])
+def test_labels_and_host_outputs_with_rerun_waves(cb, slots):
+    """Waves deeper than the first are traversed again at the end of the call
+    (host-driven rounds); their host copies and label rows are rewritten.
+    With one cluster per wave the label groups span many waves."""
+    off, adj = I.path(240)
+    g = cb.Graph(off, adj)
+    base = [np.array([120, 121], np.int32), np.array([0, 1], np.int32), np.array([60], np.int32),
+            np.array([239, 238], np.int32)]
+    clusters = base * 10  # 40 clusters: groups of 32 / slots waves, a ragged last group
+    C, n, d = len(clusters), g.n, 2
+    L = cb.Labels(n, C, d)
+    hd = torch.empty((C, n), dtype=torch.uint8).pin_memory()
+    hm = torch.empty((C, d, n), dtype=torch.int64).pin_memory()
+    g.run_batched_labels(clusters, d, L, dist=hd, masks=hm, tune={"slots": slots})
+    od = np.zeros((C, n), np.uint8)
+    om = np.zeros((C, d, n), np.uint64)
+    for c, S in enumerate(clusters):
+        od[c], om[c] = O.cbfs_alg1(off, adj, S, d)
+    assert (hd.numpy() == od).all() and (hm.numpy().view(np.uint64) == om).all()
+    L2 = cb.Labels(n, C, d)
+    g.run_batched_labels(clusters, d, L2, tune={"slots": slots})  # labels only (ring of wave buffers)
+    L3 = cb.Labels(n, C, d)
+    L3.append(torch.from_numpy(od).cuda(), torch.from_numpy(om.view(np.int64)).cuda(), [len(S) for S in clusters])
+    ref = valid_columns(rows_of(L3, n), C, C, d)
+    assert (valid_columns(rows_of(L, n), C, C, d) == ref).all()
+    assert (valid_columns(rows_of(L2, n), C, C, d) == ref).all()
