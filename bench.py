@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-single-compare", dest="single_compare", action="store_false",
                     help="skip timing the clusters one call each")
     ap.add_argument("--fixed-tune", default="", help="'alpha,slots' instead of the autotuner (profiling runs)")
+    ap.add_argument("--no-next", dest="next_rows", action="store_false",
+                    help="skip the single-source BFS comparison and the d sweep")
     return ap.parse_args()
 
 
@@ -227,6 +229,135 @@ def ncu_traffic(kernel: str):
     return e.get("dram_bytes_per_launch")
 
 
+# ------------------------------------------------- single-source BFS and d
+
+
+def timed_ms(fn, reps: int = 3) -> float:
+    """Median wall time of fn() (each call synchronises its stream)."""
+    import torch
+
+    fn()
+    out = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        out.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(out)
+
+
+def comparison_clusters(off, adj, seed: int, count: int = 10):
+    """The microbenchmark clusters of Section 5.1: a vertex and up to 63 of
+    its neighbours (d = 2)."""
+    return I.star_clusters(off, adj, count, seed=seed, size="max", min_deg=63)
+
+
+def seq_bfs_sample(off, adj, seed: int, sample: int = 8):
+    """Plain sequential BFS (the paper's "Seq-BFS" baseline) on one host core:
+    the oracle's BFS from a sample of the comparison clusters' sources, in ms
+    per 64 sources.  Part of the CPU baseline; runs before CUDA starts."""
+    import oracle
+
+    oracle.build()
+    clusters, _ = comparison_clusters(off, adj, seed)
+    t0 = time.perf_counter()
+    done = 0
+    for S in clusters[:2]:
+        for s in S[:sample // 2]:
+            oracle.bfs(off, adj, int(s))
+            done += 1
+    ms = (time.perf_counter() - t0) * 1e3 / max(done, 1) * 64
+    return {"ms_per_64_sources": round(ms, 1), "cores": 1, "kind": "oracle",
+            "sample": f"{done} plain BFSs (oracle) from the comparison clusters' sources, scaled to 64"}
+
+
+def bfs_comparison(g, off, adj, seed: int, seq=None):
+    """The paper's microbenchmark framing (Section 5.1) on this GPU: C-BFS of
+    a 64-vertex star cluster (d = 2) against the plain BFSs of its sources,
+    both through the same kernels (a BFS is C-BFS with k = 1, d = 0,
+    direction-optimising as in Algorithm "EdgeMap")."""
+    clusters, d = comparison_clusters(off, adj, seed)
+    deg = np.diff(off)
+    cb_ms, bfs_ms, bfs8_ms = [], [], []
+    for S in clusters:
+        singles = [np.array([s], np.int32) for s in S]
+        cb_ms.append(timed_ms(lambda: g.run_batched([S], d, tune={"slots": 1})))
+        bfs_ms.append(timed_ms(lambda: g.run_batched(singles, 0, tune={"slots": 1})))
+        bfs8_ms.append(timed_ms(lambda: g.run_batched(singles, 0, tune={"slots": 8})))
+    # undirected edges of the reached component (the same for every source of a cluster)
+    hd, _ = g.run([int(clusters[0][0])], 0)
+    comp_edges = int(deg[hd.cpu().numpy() != 255].sum()) // 2
+    cb, bf, b8 = statistics.mean(cb_ms), statistics.mean(bfs_ms), statistics.mean(bfs8_ms)
+    k = statistics.mean(len(S) for S in clusters)
+    out = {"clusters": len(clusters), "mean_sources": round(k, 1), "d": d,
+           "cbfs_ms_per_cluster": round(cb, 3),
+           "bfs_per_source_ms_one_per_wave": round(bf, 3),
+           "bfs_per_source_ms_eight_per_wave": round(b8, 3),
+           "bit_level_gain": round(bf / cb, 2),
+           "bfs_gteps_one_per_wave": round(k * comp_edges / (bf / 1e3) / 1e9, 3),
+           "cbfs_gteps": round(k * comp_edges / (cb / 1e3) / 1e9, 3)}
+    if seq:
+        out["speedup_over_seq_bfs"] = round(seq["ms_per_64_sources"] * k / 64 / cb, 1)
+    return out
+
+
+def d_sweep(cbfs, g, off, adj, seed: int, per_d: int = 8, ds=(2, 3, 4, 5, 6), min_deg: int = 1):
+    """C-BFS cost against the diameter bound d (Theorem 1: work grows with d):
+    per d, clusters of 64 vertices within d of each other by construction
+    (``inputs.radius_cluster`` around random centres, hop counts from this
+    library's own BFS), each run alone and batched.  The exact diameters,
+    decoded from the outputs, are reported beside d.  (On a power-law graph
+    hubs keep every cluster's spread small, so the cost hardly moves; the
+    road grid shows the growth.)"""
+    import torch
+
+    deg = np.diff(off)
+    cand = np.flatnonzero(deg >= max(min_deg, 1))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for d in ds:
+        clusters = []
+        for _ in range(50 * per_d):
+            if len(clusters) == per_d:
+                break
+            ctr = int(cand[rng.integers(0, cand.size)])
+            hd, _ = g.run([ctr], 0)
+            hops = hd.cpu().numpy().astype(np.int64)
+            hops[hops == 255] = -1
+            S = I.radius_cluster(hops, ctr, d, k=64, seed=int(rng.integers(1 << 62)))
+            if S.size >= 2:  # small balls (a grid at small d) give fewer than 64
+                clusters.append(S)
+        ks = [int(S.size) for S in clusters]
+        alone = statistics.mean(timed_ms(lambda: g.run_batched([S], d, tune={"slots": 1})) for S in clusters)
+        dist, masks = g.run_batched(clusters, d, tune={"slots": 4})
+        batched = timed_ms(lambda: g.run_batched(clusters, d, dist, masks, tune={"slots": 4}))
+        st = g.output_stats(dist, masks, ks, d)
+        # exact diameters: delta_j(S[i]) = Delta + offset of bit j at vertex S[i]
+        diam = []
+        dist_h = dist.cpu().numpy()
+        masks_h = masks.cpu().numpy().view(np.uint64)
+        for c, S in enumerate(clusters):
+            best = 0
+            for v in S:
+                seen = np.uint64(0)
+                for t in range(d):
+                    m = masks_h[c, t, v]
+                    if m & ~seen:
+                        best = max(best, int(dist_h[c, v]) + t)
+                    seen |= m
+                if seen != np.uint64((1 << ks[c]) - 1):
+                    best = max(best, int(dist_h[c, v]) + d)
+            diam.append(best)
+        out[str(d)] = {"mean_sources": round(statistics.mean(ks), 1),
+                       "ms_per_cluster_alone": round(alone, 3), "ms_per_cluster_batched": round(batched / len(clusters), 3),
+                       "arcs_scanned_per_cluster": int(st[:, 1].mean()), "rounds": int(st[:, 3].max()),
+                       "exact_diameters": sorted(set(diam))}
+        del dist, masks
+        torch.cuda.empty_cache()
+    return {"clusters_per_d": per_d, "sizes": 64, "by_d": out}
+
+
 # ---------------------------------------------------------------- arms
 
 
@@ -270,6 +401,8 @@ def run_cbfs(args, ws, rank, local):
         cpu = {"value": round(g_cpu, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                "sample": f"{done} of the {C} clusters ({wall:.1f} s wall), Algorithm 1 in plain C, "
                          f"one cluster per host core"}
+        if args.next_rows:
+            cpu["seq_bfs"] = seq_bfs_sample(off, adj, seed=rank_seed(rank) + 21)
 
     import torch
 
@@ -407,6 +540,18 @@ def run_cbfs(args, ws, rank, local):
              "qps": round(qtot / q_wall, 1), "requests": len(lat), "clusters": C,
              "mode": "one request at a time, sizes U{1..65536}, pinned H2D + kernel + D2H"}
 
+    # single-source BFS comparison and the d sweep (the same resident graph)
+    nxt = None
+    if args.next_rows and rank == 0:
+        nxt = {"bfs_comparison": bfs_comparison(g, off, adj, seed=rank_seed(rank) + 21,
+                                                seq=cpu.get("seq_bfs") if cpu else None)}
+        # centres of degree >= 63 so that even d = 2, 3 clusters have 64 vertices
+        sweep = {f"rmat_s{args.scale}": d_sweep(cbfs, g, off, adj, seed=rank_seed(rank) + 22, min_deg=63)}
+        goff, gadj = I.road_grid(1024, seed=I.MASTER_SEED + 2)
+        with cbfs.Graph(goff, gadj) as gg:
+            sweep["road_grid_1024"] = d_sweep(cbfs, gg, goff, gadj, seed=rank_seed(rank) + 23)
+        nxt["d_sweep"] = sweep
+
     # serving (continuous batching) over labels of 60 degree-ordered clusters of the same graph
     serving = None
     if args.serve_s > 0:
@@ -513,6 +658,7 @@ def run_cbfs(args, ws, rank, local):
             "query": query,
             "serving": serving,
             "one_cluster_per_launch": one,
+            "next": nxt,
         }
         print(json.dumps(line), flush=True)
     if pg:

@@ -312,6 +312,10 @@ __global__ void k_seed(Wave w, const uint64_t* seeds, int count) {
         const uint64_t e = seeds[i];
         const int s = (int)((e >> 40) & 0xFF), j = (int)((e >> 32) & 0xFF);
         const uint32_t v = (uint32_t)e;
+        if ((int64_t)v >= w.n || s >= w.P || j >= 64) {  // never for seeds staged by the host
+            set_status(w.status, CBFS_E_INVALID);
+            continue;
+        }
         w.acc[(size_t)v * w.P + s] = 1ull << j;  // (v, s) is unique within a wave
         if (atomicExch(w.rq + v, 1u) != 1u) {
             append(w.q0, &w.ctl[0].qlen, v);
@@ -335,6 +339,7 @@ __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count, int bo
         const uint64_t e = seeds[i];
         const int s = (int)((e >> 40) & 0xFF);
         const uint32_t v = (uint32_t)e;
+        if ((int64_t)v >= w.n || s >= w.P) continue;  // flagged by k_seed
         if (w.vis[(size_t)v * w.P + s] != w.slots[s].all) set_status(w.status, CBFS_E_DIAMETER);
     }
 }
@@ -1242,6 +1247,14 @@ int slots_for(const cbfs_tune_t* tune, int C) {
     return p2;
 }
 
+// Forgets every captured graph of the handle (and the call shapes seen once).
+void drop_graphs(cbfs_graph_s* g) {
+    if (!g->graphs.empty()) cudaDeviceSynchronize();  // a replay may still be in flight
+    for (auto& ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+    g->graphs.clear();
+    g->seen.clear();
+}
+
 // True when p is host memory (pinned or pageable): kernels do not write it.
 bool is_host_pointer(const void* p) {
     cudaPointerAttributes a;
@@ -1329,10 +1342,14 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         if (!d) return nullptr;
         return staged ? stage_masks + (size_t)(wv % G) * (size_t)wave_masks : masks + (size_t)wv * (size_t)wave_masks;
     };
+    // Captured graphs hold these device pointers: when one of them moves, every
+    // cached graph goes (a replay would read the freed buffer).
+    const void* held[2] = {g->slots, g->seeds};
     rc = ensure_dev(&g->slots, &g->slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_pinned(&g->h_slots, &g->h_slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_dev(&g->seeds, &g->seeds_cap, total_src);
     if (!rc) rc = ensure_pinned(&g->h_seeds, &g->h_seeds_cap, total_src);
+    if (held[0] != (const void*)g->slots || held[1] != (const void*)g->seeds) drop_graphs(g);
     if (rc) return rc;
     // slot tables and seeds of every wave, staged once
     std::vector<int64_t> wave_seed_off(nwaves + 1, 0);
@@ -1424,6 +1441,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         }
         key = fnv1a(key, wave_seed_off.data(), sizeof(int64_t) * wave_seed_off.size());
         key = fnv1a(key, &grid, sizeof(grid));
+        key = fnv1a(key, &g->seeds, sizeof(g->seeds));  // baked into k_seed / k_check_sources
         cudaGraphExec_t exec = nullptr;
         for (size_t i = 0; i < g->graphs.size(); ++i) {
             if (g->graphs[i].key == key) {

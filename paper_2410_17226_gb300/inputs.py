@@ -35,6 +35,9 @@ returned beside it):
 * ``ball_clusters``: a random centre plus the next k-1 vertices in BFS order
   from it; d = the exact diameter of that set (at most twice the BFS level
   of the last one taken).
+* ``radius_cluster``: a cluster whose diameter is at most a given d, drawn
+  from hop counts to a centre that the caller supplies (the d-sweep
+  workload; the hop counts come from whichever BFS the caller trusts).
 """
 from __future__ import annotations
 
@@ -194,9 +197,10 @@ def degrees(off) -> np.ndarray:
     return off[1:] - off[:-1]
 
 
-def star_clusters(off, adj, count: int, seed: int, size: str = "max", kmax: int = 64):
-    """``count`` star clusters: a uniform random non-isolated centre plus a
-    uniform random subset of its neighbours, drawn without replacement.
+def star_clusters(off, adj, count: int, seed: int, size: str = "max", kmax: int = 64, min_deg: int = 1):
+    """``count`` star clusters: a uniform random centre of degree >= min_deg
+    (default: any non-isolated vertex) plus a uniform random subset of its
+    neighbours, drawn without replacement.
 
     ``size="max"``: as many neighbours as fit (k = min(kmax, 1 + deg)).
     ``size="uniform"``: k uniform in 1..kmax, capped at 1 + deg.
@@ -204,7 +208,7 @@ def star_clusters(off, adj, count: int, seed: int, size: str = "max", kmax: int 
     is a valid bound; callers may pass it as is).
     """
     deg = degrees(off)
-    cand = np.flatnonzero(deg > 0)
+    cand = np.flatnonzero(deg >= max(min_deg, 1))
     if cand.size == 0:
         raise ValueError("graph has no edges")
     g = _gen(seed)
@@ -314,6 +318,39 @@ def ball_clusters(off, adj, count: int, k: int, seed: int, dmax: int = 15, max_t
         clusters.append(np.asarray(taken, dtype=np.int32))
         ds.append(int(diam))
     return clusters, ds
+
+
+def radius_cluster(hops, centre: int, d: int, k: int = 64, seed: int = 0) -> np.ndarray:
+    """k distinct vertices (the centre first) whose pairwise hop counts are at
+    most d by construction, given ``hops`` = hop counts from ``centre`` (any
+    negative value = unreachable).
+
+    With r = d // 2, members lie within r hops of the centre, so any two are
+    at most 2r apart; half of them (when there are enough) are drawn at
+    exactly r hops to spread the set.  For odd d one more member is taken at
+    r + 1 hops, at most r + (r + 1) = d from every other.  Fewer than k
+    vertices come back when the ball is smaller.
+    """
+    hops = np.asarray(hops)
+    g = _gen(seed)
+    r = d // 2
+    inner = np.flatnonzero((hops >= 1) & (hops < r))
+    rim = np.flatnonzero(hops == r) if r >= 1 else np.zeros(0, np.int64)
+    want = k - 1 - (d % 2)
+
+    def draw(pool, m):
+        m = int(min(m, pool.size))
+        if m <= 0:
+            return np.zeros(0, np.int64)
+        keys = _raw(g, pool.size)
+        return np.sort(pool[np.argsort(keys, kind="stable")[:m]])
+
+    from_rim = draw(rim, max(want // 2, want - inner.size))
+    from_inner = draw(inner, want - from_rim.size)
+    out = [np.array([centre], np.int64), from_rim, from_inner]
+    if d % 2 == 1:
+        out.append(draw(np.flatnonzero(hops == r + 1), 1))
+    return np.concatenate(out).astype(np.int32)
 
 
 def random_pairs(n: int, q: int, seed: int) -> np.ndarray:

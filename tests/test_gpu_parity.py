@@ -232,3 +232,23 @@ def test_output_stats_match_oracle_counters(cb):
     for c, S in enumerate(clusters):
         _, _, cnt = O.cbfs_alg1(off, adj, S, d, with_counters=True)
         assert st[c].tolist() == [cnt["V"], cnt["A"], cnt["reached_arcs"], cnt["rounds"]]
+
+
+def test_graph_replay_after_the_seed_buffer_grows(cb):
+    """Cached CUDA graphs hold the seed buffer's address: a larger call that
+    reallocates it must retire them, and later calls of an old shape with
+    new sources must still be exact."""
+    off, adj = I.rmat(12, seed=8)
+    g = cb.Graph(off, adj)
+    deg = np.diff(off)
+    order = np.argsort(-deg, kind="stable")
+    small = [np.array([int(order[i])] + [int(x) for x in adj[off[order[i]]:off[order[i]] + 4]], np.int32)
+             for i in (10, 20, 30)]
+    big = [np.array([int(order[0])] + [int(x) for x in adj[off[order[0]]:off[order[0]] + 40]], np.int32)]
+    for S in (small[0], small[0], small[0]):  # first sighting, capture, replay
+        dd, dm = g.run_batched([S], 2)
+    g.run_batched(big * 3, 2)  # more seeds than ever: the buffer moves
+    for S in (small[1], small[1], small[2]):
+        dd, dm = g.run_batched([S], 2)
+        od, om = O.cbfs_alg1(off, adj, S, 2)
+        assert (dd[0].cpu().numpy() == od).all() and (cb.as_numpy_u64(dm[0]) == om).all()

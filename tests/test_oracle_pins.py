@@ -388,3 +388,24 @@ def test_label_rows_layout():
         assert (rows[v, :C] == dist[:, v]).all() and (rows[v, C:P] == 0).all()
         blk = rows[v, P:].view(np.uint64).reshape(d, C)
         assert (blk == masks[:, :, v].T).all()
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6])
+def test_radius_cluster_diameter_bound(d):
+    """The d-sweep clusters: every pair of members within d hops (checked by
+    BFS from each member), centre first, distinct, and for odd d one member
+    at (d + 1) / 2 hops from the centre."""
+    off, adj = I.rmat(10, seed=3)
+    deg = np.diff(off)
+    cand = np.flatnonzero(deg > 0)
+    rng = np.random.default_rng(d)
+    for _ in range(4):
+        ctr = int(cand[rng.integers(0, cand.size)])
+        hops = O.bfs(off, adj, ctr)
+        S = I.radius_cluster(hops, ctr, d, k=64, seed=5)
+        assert S[0] == ctr and len(set(S.tolist())) == S.size <= 64
+        for v in S:
+            hv = O.bfs(off, adj, int(v))
+            assert (hv[S] >= 0).all() and hv[S].max() <= d
+        if d % 2 and (hops == d // 2 + 1).any():
+            assert (hops[S] == d // 2 + 1).sum() == 1
