@@ -358,6 +358,55 @@ def d_sweep(cbfs, g, off, adj, seed: int, per_d: int = 8, ds=(2, 3, 4, 5, 6), mi
     return {"clusters_per_d": per_d, "sizes": 64, "by_d": out}
 
 
+def ll_quality(cbfs, g, off, adj, seed: int, budget: int = 1024, n_src: int = 32, pairs_per_src: int = 3125):
+    """Landmark-labeling index quality against word size (Section 5.3,
+    table "ApproxLL" on this synthetic graph): plain landmarks and clusters of
+    w = 8, 16, 32, 64 (d = 2) under one budget of bytes per vertex; index
+    time, label bytes, distortion epsilon over 100,000 pairs of the largest
+    component and query time.  Exact distances come from this library's BFS
+    (k = 1, d = 0) from each pair's first vertex."""
+    import torch
+
+    from paper_2410_17226_gb300 import ll
+
+    n = off.size - 1
+    deg = np.diff(off)
+    hub = int(np.argmax(deg))
+    comp_d, _ = g.run([hub], 0)
+    comp = np.flatnonzero(comp_d.cpu().numpy() != 255)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    us = comp[rng.integers(0, comp.size, n_src)].astype(np.int32)
+    tru, _ = g.run_batched([np.array([u], np.int32) for u in us], 0, tune={"slots": 8})
+    tru = tru.cpu().numpy()
+    vs = comp[rng.integers(0, comp.size, (n_src, pairs_per_src))]
+    pairs = np.stack([np.repeat(us, pairs_per_src), vs.reshape(-1)], axis=1).astype(np.int32)
+    exact = tru[np.repeat(np.arange(n_src), pairs_per_src), vs.reshape(-1)].astype(np.int64)
+    exact[exact == 255] = -1
+    pairs_dev = torch.from_numpy(pairs).cuda()
+    out = {}
+    for name, w in (("plain", 1), ("w8", 8), ("w16", 16), ("w32", 32), ("w64", 64)):
+        clusters, d = ll.select(off, adj, budget, w=w)
+        L, build_ms = ll.build(g, clusters, d, w)
+        ans = L.query(pairs_dev)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        L.query(pairs_dev, out=ans)
+        e1.record()
+        torch.cuda.synchronize()
+        q_ms = e0.elapsed_time(e1)
+        dd = ll.distortion(cbfs.as_numpy_u16(ans), exact)
+        out[name] = {"clusters": len(clusters), "landmarks": int(sum(len(S) for S in clusters)), "d": d,
+                     "row_bytes_per_vertex": cbfs.Labels.bytes_per_vertex(len(clusters), d, max(w, 8) if d else 64),
+                     "index_ms": round(build_ms, 2), "epsilon_pct": round(100 * dd["epsilon"], 3),
+                     "exact_share": round(dd["exact_share"], 4), "unanswered": dd["unanswered"],
+                     "query_ns_per_pair": round(q_ms * 1e6 / len(pairs), 2)}
+        L.close()
+        torch.cuda.empty_cache()
+    return {"budget_bytes_per_vertex": budget, "pairs": int(len(pairs)), "sources_of_pairs": n_src,
+            "pairs_from": "the component of the highest-degree vertex", "by_index": out}
+
+
 # ---------------------------------------------------------------- arms
 
 
@@ -551,6 +600,7 @@ def run_cbfs(args, ws, rank, local):
         with cbfs.Graph(goff, gadj) as gg:
             sweep["road_grid_1024"] = d_sweep(cbfs, gg, goff, gadj, seed=rank_seed(rank) + 23)
         nxt["d_sweep"] = sweep
+        nxt["ll_quality"] = ll_quality(cbfs, g, off, adj, seed=rank_seed(rank) + 24)
 
     # serving (continuous batching) over labels of 60 degree-ordered clusters of the same graph
     serving = None

@@ -221,6 +221,18 @@ int cbfs_profile(cbfs_graph_t g, int enable, cbfs_kernel_times_t* host_out);
  * hbm_budget_bytes (0 = no budget) or the allocation fails.
  */
 int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes, cbfs_labels_t* out);
+
+/*
+ * cbfs_labels_create with w-bit subset words, w in {8, 16, 32, 64}: the
+ * store then holds clusters of at most w sources (the word sizes of the
+ * paper's landmark-labeling study, Section 5.3), 1 + d * w / 8 bytes per
+ * cluster and vertex.  Row layout: [dist C_capacity bytes | pad to 8 |
+ * d blocks of round_up(C_capacity * w / 8, 8) bytes].  Appends narrow the
+ * C-BFS output words (whose bits at and above the cluster size are zero)
+ * and reject clusters larger than w with CBFS_E_INVALID.  w = 64 is
+ * cbfs_labels_create.
+ */
+int cbfs_labels_create_w(int64_t n, int C_capacity, int d, int w, size_t hbm_budget_bytes, cbfs_labels_t* out);
 int cbfs_labels_destroy(cbfs_labels_t L);
 
 /*

@@ -67,6 +67,7 @@ SIGNATURES = {
     "cbfs_output_stats": (_I, [_P, _P, _P, _P, _I, _I, _P, _P]),
     "cbfs_profile": (_I, [_P, _I, _P]),
     "cbfs_labels_create": (_I, [_I64, _I, _I, _SZ, _P]),
+    "cbfs_labels_create_w": (_I, [_I64, _I, _I, _I, _SZ, _P]),
     "cbfs_labels_destroy": (_I, [_P]),
     "cbfs_labels_append": (_I, [_P, _P, _P, _P, _I, _P]),
     "cbfs_labels_reset": (_I, [_P]),
@@ -297,14 +298,21 @@ def run_noalloc(off: torch.Tensor, adj: torch.Tensor, sources, d: int, dist: tor
 
 
 class Labels:
-    """Vertex-major landmark labels on the GPU and the distance query."""
+    """Vertex-major landmark labels on the GPU and the distance query.
+    ``w`` (8, 16, 32, 64) is the subset word width: clusters of at most w
+    sources, 1 + d * w / 8 bytes per cluster and vertex."""
 
-    def __init__(self, n: int, capacity: int, d: int, budget_bytes: int = 0):
+    def __init__(self, n: int, capacity: int, d: int, budget_bytes: int = 0, w: int = 64):
         _require_cuda()
         self._h = ctypes.c_void_p()
-        _check(lib().cbfs_labels_create(int(n), int(capacity), int(d), int(budget_bytes), ctypes.byref(self._h)),
-               "cbfs_labels_create")
-        self.n, self.capacity, self.d = int(n), int(capacity), int(d)
+        _check(lib().cbfs_labels_create_w(int(n), int(capacity), int(d), int(w), int(budget_bytes),
+                                          ctypes.byref(self._h)), "cbfs_labels_create_w")
+        self.n, self.capacity, self.d, self.w = int(n), int(capacity), int(d), int(w)
+
+    @staticmethod
+    def bytes_per_vertex(capacity: int, d: int, w: int = 64) -> int:
+        """Row size of a store (the layout of ``cbfs_labels_create_w``)."""
+        return (capacity + 7) // 8 * 8 + d * ((capacity * w // 8 + 7) // 8 * 8)
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -2,9 +2,12 @@
 //
 // Label store: one row per vertex v (the L[v][.] of Algorithm "Framework of
 // Landmark Labeling"), holding for every stored cluster c the byte
-// Delta_v(c) and the words S_v[0..d-1](c):
-//   [ dist: Ccap bytes | pad to P = round_up(Ccap, 8) | d blocks of Ccap u64 ]
-// so one query reads two contiguous rows.
+// Delta_v(c) and the subsets S_v[0..d-1](c) as w-bit words (w = 8, 16, 32 or
+// 64: clusters of at most w sources, Section 5.3's word sizes):
+//   [ dist: Ccap bytes | pad to P = round_up(Ccap, 8)
+//     | d blocks of round_up(Ccap * w / 8, 8) bytes ]
+// so one query reads two contiguous rows.  A cluster costs 1 + d * w / 8
+// bytes per vertex (17 for w = 64, d = 2; 3 for w = 8).
 //
 // Query (Section 4.2, "Answering Queries with Clustered Landmarks"): for a
 // cluster, the distance through its best landmark is Delta_u + Delta_v + t
@@ -23,8 +26,10 @@ struct cbfs_labels_s {
     int64_t n = 0;
     int cap = 0;
     int d = 0;
+    int wb = 8;  // bytes per subset word (w / 8)
     int count = 0;
-    int64_t P = 0;
+    int64_t P = 0;      // offset of the first subset block
+    int64_t block = 0;  // bytes per subset block
     int64_t stride = 0;
     uint8_t* rows = nullptr;
     uint64_t* alls = nullptr;  // [cap]
@@ -37,8 +42,10 @@ namespace {
 constexpr int kTV = 64;  // vertices per transpose tile
 constexpr int kTC = 32;  // clusters per transpose tile
 
-// Cluster-major outputs -> vertex-major rows for clusters [c0, c0 + C).
-__global__ void __launch_bounds__(256) k_labels_append(int64_t n, int d, int C, int c0, int cap, int64_t P,
+// Cluster-major outputs -> vertex-major rows for clusters [c0, c0 + C);
+// subset words narrowed to T (their bits above the cluster size are zero).
+template <class T>
+__global__ void __launch_bounds__(256) k_labels_append(int64_t n, int d, int C, int c0, int64_t P, int64_t block,
                                                        int64_t stride, const uint8_t* dist, const uint64_t* masks,
                                                        uint8_t* rows) {
     __shared__ uint64_t tm[kTC][kTV + 1];
@@ -68,8 +75,8 @@ __global__ void __launch_bounds__(256) k_labels_append(int64_t n, int d, int C, 
         for (int i = threadIdx.x; i < kTC * kTV; i += blockDim.x) {
             const int vv = i / kTC, c = i % kTC;
             if (c < nc && vv < nv) {
-                uint64_t* dst = reinterpret_cast<uint64_t*>(rows + (v0 + vv) * stride + P) + (size_t)s * cap + c0 + cb + c;
-                *dst = tm[c][vv];
+                T* dst = reinterpret_cast<T*>(rows + (v0 + vv) * stride + P + s * block) + c0 + cb + c;
+                *dst = (T)tm[c][vv];
             }
         }
     }
@@ -80,7 +87,8 @@ __global__ void __launch_bounds__(256) k_labels_append(int64_t n, int d, int C, 
 // so the lanes of a warp fill whole runs of each row while reading nc
 // coalesced streams.  (The tile transpose above would leave most of its
 // 32-cluster tile idle.)
-__global__ void __launch_bounds__(256) k_labels_wave(int64_t n, int d, int nc, int pos, int cap, int64_t P,
+template <class T>
+__global__ void __launch_bounds__(256) k_labels_wave(int64_t n, int d, int nc, int pos, int64_t P, int64_t block,
                                                      int64_t stride, const uint8_t* dist, const uint64_t* masks,
                                                      uint8_t* rows) {
     const int64_t total = n * nc;
@@ -89,8 +97,8 @@ __global__ void __launch_bounds__(256) k_labels_wave(int64_t n, int d, int nc, i
         const int c = (int)(t - v * nc);
         uint8_t* row = rows + v * stride;
         row[pos + c] = dist[(size_t)c * (size_t)n + v];
-        uint64_t* m = reinterpret_cast<uint64_t*>(row + P) + pos + c;
-        for (int s = 0; s < d; ++s) m[(size_t)s * cap] = masks[((size_t)c * (size_t)d + s) * (size_t)n + v];
+        for (int s = 0; s < d; ++s)
+            reinterpret_cast<T*>(row + P + s * block)[pos + c] = (T)masks[((size_t)c * (size_t)d + s) * (size_t)n + v];
     }
 }
 
@@ -119,8 +127,8 @@ __device__ __forceinline__ int best_offset_any(const uint64_t* su, const uint64_
     return -1;
 }
 
-template <int D>
-__global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int cap, int64_t P, int64_t stride,
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int64_t P, int64_t block, int64_t stride,
                                                const uint8_t* rows, const uint64_t* alls, const int32_t* pairs,
                                                int64_t q, uint16_t* out, int* status) {
     const int lane = threadIdx.x & 31;
@@ -142,8 +150,6 @@ __global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int cap,
         }
         const uint8_t* ru = rows + (int64_t)u * stride;
         const uint8_t* rv = rows + (int64_t)v * stride;
-        const uint64_t* mu = reinterpret_cast<const uint64_t*>(ru + P);
-        const uint64_t* mv = reinterpret_cast<const uint64_t*>(rv + P);
         int best = 0x7fffffff;
         for (int c = lane; c < C; c += 32) {
             const int du = ru[c], dv = rv[c];
@@ -154,8 +160,8 @@ __global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int cap,
 #pragma unroll
             for (int i = 0; i < DM - 1; ++i) {
                 if (i < dd) {
-                    su[i] = __ldg(mu + (size_t)i * cap + c);
-                    sv[i] = __ldg(mv + (size_t)i * cap + c);
+                    su[i] = (uint64_t)__ldg(reinterpret_cast<const T*>(ru + P + i * block) + c);
+                    sv[i] = (uint64_t)__ldg(reinterpret_cast<const T*>(rv + P + i * block) + c);
                     ou |= su[i];
                     ov |= sv[i];
                 }
@@ -172,6 +178,48 @@ __global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int cap,
     }
 }
 
+// Launch helpers for the store's word width.
+void append_rows(const cbfs_labels_s* L, const uint8_t* dist, const uint64_t* masks, int C, int pos, cudaStream_t st) {
+    if (C <= 8) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, L->device);
+        const unsigned blocks = (unsigned)std::min<int64_t>((L->n * C + 255) / 256, (int64_t)std::max(sms, 1) * 8);
+#define CBFS_WAVE(T) k_labels_wave<T><<<blocks, 256, 0, st>>>(L->n, L->d, C, pos, L->P, L->block, L->stride, dist, masks, L->rows)
+        switch (L->wb) {
+            case 1: CBFS_WAVE(uint8_t); break;
+            case 2: CBFS_WAVE(uint16_t); break;
+            case 4: CBFS_WAVE(uint32_t); break;
+            default: CBFS_WAVE(uint64_t); break;
+        }
+#undef CBFS_WAVE
+    } else {
+        dim3 grid((unsigned)((L->n + kTV - 1) / kTV), (unsigned)((C + kTC - 1) / kTC));
+#define CBFS_TILE(T) k_labels_append<T><<<grid, 256, 0, st>>>(L->n, L->d, C, pos, L->P, L->block, L->stride, dist, masks, L->rows)
+        switch (L->wb) {
+            case 1: CBFS_TILE(uint8_t); break;
+            case 2: CBFS_TILE(uint16_t); break;
+            case 4: CBFS_TILE(uint32_t); break;
+            default: CBFS_TILE(uint64_t); break;
+        }
+#undef CBFS_TILE
+    }
+}
+
+template <int D>
+void query_rows(const cbfs_labels_s* L, unsigned blocks, const int32_t* pairs, int64_t q, uint16_t* out,
+                cudaStream_t st) {
+#define CBFS_QUERY(T)                                                                                              \
+    k_query<D, T><<<blocks, 256, 0, st>>>(L->n, L->d, L->count, L->P, L->block, L->stride, L->rows, L->alls, pairs, \
+                                          q, out, L->status)
+    switch (L->wb) {
+        case 1: CBFS_QUERY(uint8_t); break;
+        case 2: CBFS_QUERY(uint16_t); break;
+        case 4: CBFS_QUERY(uint32_t); break;
+        default: CBFS_QUERY(uint64_t); break;
+    }
+#undef CBFS_QUERY
+}
+
 }  // namespace
 
 namespace cbfs {
@@ -182,7 +230,7 @@ int labels_reserve(cbfs_labels_s* L, int64_t n, int d, const int32_t* coff, int 
     std::vector<uint64_t> alls((size_t)std::max(C, 1));
     for (int c = 0; c < C; ++c) {
         const int k = coff[c + 1] - coff[c];
-        if (k < 1 || k > 64) return CBFS_E_INVALID;
+        if (k < 1 || k > 8 * L->wb) return CBFS_E_INVALID;
         alls[c] = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
     }
     cudaSetDevice(L->device);
@@ -198,16 +246,7 @@ void labels_rollback(cbfs_labels_s* L, int base) { L->count = base; }
 cudaError_t labels_write(cbfs_labels_s* L, const uint8_t* dist, const uint64_t* masks, int C, int pos,
                          cudaStream_t st) {
     if (L->n == 0 || C == 0) return cudaSuccess;
-    if (C <= 8) {
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, L->device);
-        const int64_t blocks = std::min<int64_t>((L->n * C + 255) / 256, (int64_t)std::max(sms, 1) * 8);
-        k_labels_wave<<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, C, pos, L->cap, L->P, L->stride, dist, masks,
-                                                        L->rows);
-    } else {
-        dim3 grid((unsigned)((L->n + kTV - 1) / kTV), (unsigned)((C + kTC - 1) / kTC));
-        k_labels_append<<<grid, 256, 0, st>>>(L->n, L->d, C, pos, L->cap, L->P, L->stride, dist, masks, L->rows);
-    }
+    append_rows(L, dist, masks, C, pos, st);
     return cudaGetLastError();
 }
 
@@ -215,8 +254,9 @@ cudaError_t labels_write(cbfs_labels_s* L, const uint8_t* dist, const uint64_t* 
 
 extern "C" {
 
-int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes, cbfs_labels_t* out) {
+int cbfs_labels_create_w(int64_t n, int C_capacity, int d, int w, size_t hbm_budget_bytes, cbfs_labels_t* out) {
     if (!out || n < 0 || n >= (int64_t)0x7fffffff || C_capacity < 1 || d < 0 || d > 15) return CBFS_E_INVALID;
+    if (w != 8 && w != 16 && w != 32 && w != 64) return CBFS_E_INVALID;
     *out = nullptr;
     cbfs_labels_s* L = new (std::nothrow) cbfs_labels_s();
     if (!L) return CBFS_E_NOMEM;
@@ -224,8 +264,10 @@ int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes
     L->n = n;
     L->cap = C_capacity;
     L->d = d;
+    L->wb = w / 8;
     L->P = ((int64_t)C_capacity + 7) / 8 * 8;
-    L->stride = L->P + 8 * (int64_t)d * C_capacity;
+    L->block = ((int64_t)C_capacity * L->wb + 7) / 8 * 8;
+    L->stride = L->P + (int64_t)d * L->block;
     const size_t bytes = (size_t)std::max<int64_t>(n, 1) * (size_t)L->stride;
     if (hbm_budget_bytes && bytes > hbm_budget_bytes) {
         delete L;
@@ -244,6 +286,10 @@ int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes
     }
     *out = L;
     return CBFS_OK;
+}
+
+int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes, cbfs_labels_t* out) {
+    return cbfs_labels_create_w(n, C_capacity, d, 64, hbm_budget_bytes, out);
 }
 
 int cbfs_labels_destroy(cbfs_labels_t L) {
@@ -265,15 +311,14 @@ int cbfs_labels_append(cbfs_labels_t L, const uint8_t* dist, const uint64_t* mas
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<uint64_t> alls((size_t)C);
     for (int c = 0; c < C; ++c) {
-        if (host_ks[c] < 1 || host_ks[c] > 64) return CBFS_E_INVALID;
+        if (host_ks[c] < 1 || host_ks[c] > 8 * L->wb) return CBFS_E_INVALID;
         alls[c] = host_ks[c] >= 64 ? ~0ull : ((1ull << host_ks[c]) - 1ull);
     }
     // synchronous copy of the small table: the host vector dies with the call
     if (cudaMemcpy(L->alls + L->count, alls.data(), sizeof(uint64_t) * C, cudaMemcpyHostToDevice) != cudaSuccess)
         return CBFS_E_CUDA;
     if (L->n > 0) {
-        dim3 grid((unsigned)((L->n + kTV - 1) / kTV), (unsigned)((C + kTC - 1) / kTC));
-        k_labels_append<<<grid, 256, 0, st>>>(L->n, L->d, C, L->count, L->cap, L->P, L->stride, dist, masks, L->rows);
+        append_rows(L, dist, masks, C, L->count, st);
         if (cudaGetLastError() != cudaSuccess) return CBFS_E_CUDA;
     }
     L->count += C;
@@ -306,15 +351,9 @@ int cbfs_query_distance(cbfs_labels_t L, const int32_t* pairs, int64_t q, uint16
     const int64_t warps_per_block = 8;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((q + warps_per_block - 1) / warps_per_block, 152 * 16));
     switch (L->d) {
-        case 1:
-            k_query<1><<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, L->count, L->cap, L->P, L->stride, L->rows, L->alls, pairs, q, out, L->status);
-            break;
-        case 2:
-            k_query<2><<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, L->count, L->cap, L->P, L->stride, L->rows, L->alls, pairs, q, out, L->status);
-            break;
-        default:
-            k_query<0><<<(unsigned)blocks, 256, 0, st>>>(L->n, L->d, L->count, L->cap, L->P, L->stride, L->rows, L->alls, pairs, q, out, L->status);
-            break;
+        case 1: query_rows<1>(L, (unsigned)blocks, pairs, q, out, st); break;
+        case 2: query_rows<2>(L, (unsigned)blocks, pairs, q, out, st); break;
+        default: query_rows<0>(L, (unsigned)blocks, pairs, q, out, st); break;
     }
     if (cudaGetLastError() != cudaSuccess) return CBFS_E_CUDA;
     return CBFS_OK;
