@@ -6,8 +6,9 @@ its Python binding) never imports it.
 
 Everything here is a thin ctypes wrapper around ``cbfs_oracle.c``: a plain,
 sequential C restatement of the paper's definitions (Section 3.1), of
-Algorithm 1 (Section 3.2), of an exact certificate checker and of the
-landmark-labeling query (Section 4.2).  See the C file for the readings taken
+Algorithm 1 (Section 3.2), of an exact certificate checker, of the
+landmark-labeling query (Section 4.2) and of the bounded bidirectional search
+added to queries (Appendix B).  See the C file for the readings taken
 where the paper is ambiguous.
 
 Every function is pinned by ``tests/test_oracle_pins.py`` against the
@@ -59,6 +60,8 @@ def _load():
         lib.oracle_query.restype = i32
         lib.oracle_label_rows.argtypes = [i64, i32, i32, P, P, P]
         lib.oracle_label_rows.restype = i32
+        lib.oracle_local_search.argtypes = [i64, P, P, i64, P, i64, P]
+        lib.oracle_local_search.restype = i32
         _lib = lib
     return _lib
 
@@ -174,3 +177,18 @@ def label_rows(dist_cn, masks_cdn) -> np.ndarray:
     if rc:
         raise OracleError(rc, "oracle_label_rows")
     return rows[:n]
+
+
+def local_search(off, adj, pairs, tau: int) -> np.ndarray:
+    """Bounded bidirectional search (Appendix B, see ``oracle_local_search``):
+    uint16[q], 0xFFFF where the tau-vertex balls of the two ends do not meet."""
+    off, adj = _csr(off, adj)
+    n = off.size - 1
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    q = pairs.shape[0]
+    out = np.empty(max(q, 1), dtype=np.uint16)
+    rc = _load().oracle_local_search(n, _p(off), _p(adj), q, _p(pairs if q else np.zeros(2, np.int32)), int(tau),
+                                     _p(out))
+    if rc:
+        raise OracleError(rc, "oracle_local_search")
+    return out[:q]

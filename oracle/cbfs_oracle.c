@@ -32,6 +32,10 @@
  *                         "Framework of Landmark Labeling"): min over all
  *                         landmarks of delta(u,s) + delta(s,v), decoded from
  *                         the cluster outputs.
+ *   oracle_local_search   the bounded bidirectional search added to queries
+ *                         (Appendix B): BFS balls of at most tau vertices
+ *                         around u and v (whole levels), min over common
+ *                         vertices of the two hop counts.
  *
  * Return codes: 0 ok; -1 invalid argument; -2 some vertex sees source
  * distances spread wider than d (the cluster diameter bound of Corollary 1
@@ -335,4 +339,79 @@ int oracle_label_rows(int64_t n, int C, int d, const uint8_t* dist, const uint64
         }
     }
     return OR_OK;
+}
+
+/*
+ * Bounded bidirectional search of a query (Appendix B).  Around each end a
+ * BFS grows level by level and keeps a level only if the ball (the end
+ * itself included) then holds at most tau vertices; the first level that
+ * would overflow is dropped and the search stops.  For every pair, out[t] =
+ * min over vertices x in both balls of hops(u, x) + hops(v, x), 0 for u == v
+ * and 0xFFFF when the balls do not meet.  Whole levels make the balls
+ * independent of the order in which a level's vertices are found; the
+ * answer is delta(u, v) whenever it is finite (any common vertex lies on a
+ * walk of that length, and a shortest path crosses both balls' boundaries
+ * when they meet), so only its presence depends on tau.
+ */
+static int64_t ball(int64_t n, const int64_t* off, const int32_t* adj, int32_t c, int64_t tau, int32_t* hop,
+                    int32_t* list) {
+    /* hop[] must be -1 everywhere on entry; the ball's vertices are left in
+       list[0, size) with their hops set, everything else stays -1 */
+    int64_t size = 1, lo = 0;
+    list[0] = c;
+    hop[c] = 0;
+    for (int32_t h = 1;; ++h) {
+        int64_t hi = size, grown = size;
+        int overflow = 0;
+        for (int64_t i = lo; i < hi && !overflow; ++i) {
+            int32_t x = list[i];
+            for (int64_t e = off[x]; e < off[x + 1]; ++e) {
+                int32_t y = adj[e];
+                if (hop[y] >= 0) continue;
+                if (grown == tau) { overflow = 1; break; }
+                hop[y] = h;
+                list[grown++] = y;
+            }
+        }
+        if (overflow) { /* drop the partial level */
+            for (int64_t i = hi; i < grown; ++i) hop[list[i]] = -1;
+            return hi;
+        }
+        if (grown == hi) return hi; /* no new level */
+        lo = hi;
+        size = grown;
+    }
+    (void)n;
+}
+
+int oracle_local_search(int64_t n, const int64_t* off, const int32_t* adj, int64_t q, const int32_t* pairs,
+                        int64_t tau, uint16_t* out) {
+    if (n < 0 || q < 0 || tau < 1) return OR_INVALID;
+    int32_t* hu = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t* hv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t* lu = (int32_t*)malloc(sizeof(int32_t) * (size_t)(tau < n ? tau : (n > 0 ? n : 1)));
+    int32_t* lv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(tau < n ? tau : (n > 0 ? n : 1)));
+    if (!hu || !hv || !lu || !lv) {
+        free(hu); free(hv); free(lu); free(lv);
+        return OR_NOMEM;
+    }
+    for (int64_t v = 0; v < n; ++v) hu[v] = hv[v] = -1;
+    int rc = OR_OK;
+    for (int64_t t = 0; t < q; ++t) {
+        int32_t u = pairs[2 * t], v = pairs[2 * t + 1];
+        if (u < 0 || (int64_t)u >= n || v < 0 || (int64_t)v >= n) { rc = OR_INVALID; break; }
+        if (u == v) { out[t] = 0; continue; }
+        int64_t su = ball(n, off, adj, u, tau, hu, lu);
+        int64_t sv = ball(n, off, adj, v, tau, hv, lv);
+        int64_t best = -1;
+        for (int64_t i = 0; i < su; ++i) {
+            int32_t x = lu[i];
+            if (hv[x] >= 0 && (best < 0 || hu[x] + hv[x] < best)) best = hu[x] + hv[x];
+        }
+        out[t] = best < 0 ? 0xFFFF : (uint16_t)best;
+        for (int64_t i = 0; i < su; ++i) hu[lu[i]] = -1;
+        for (int64_t i = 0; i < sv; ++i) hv[lv[i]] = -1;
+    }
+    free(hu); free(hv); free(lu); free(lv);
+    return rc;
 }

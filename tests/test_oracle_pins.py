@@ -409,3 +409,60 @@ def test_radius_cluster_diameter_bound(d):
             assert (hv[S] >= 0).all() and hv[S].max() <= d
         if d % 2 and (hops == d // 2 + 1).any():
             assert (hops[S] == d // 2 + 1).sum() == 1
+
+
+def _path_ball(u, n, tau):
+    """Whole BFS levels around u on a path of n vertices, at most tau vertices."""
+    ball = {u}
+    h = 0
+    while True:
+        h += 1
+        nxt = {x for x in (u - h, u + h) if 0 <= x < n}
+        if not nxt or len(ball) + len(nxt) > tau:
+            return ball
+        ball |= nxt
+
+
+@pytest.mark.parametrize("tau", [1, 2, 3, 4, 7])
+def test_local_search_closed_form_on_a_path(tau):
+    """Appendix B's bounded bidirectional search on a path of 12 vertices:
+    the answer is |u - v| when the two whole-level balls meet, else none."""
+    n = 12
+    off, adj = I.path(n)
+    pairs = np.array([(u, v) for u in range(n) for v in range(n)], np.int32)
+    got = O.local_search(off, adj, pairs, tau)
+    for (u, v), a in zip(pairs, got):
+        if u == v:
+            assert a == 0
+        elif _path_ball(u, n, tau) & _path_ball(v, n, tau):
+            assert a == abs(u - v), (u, v, tau)
+        else:
+            assert a == 0xFFFF, (u, v, tau)
+
+
+def test_local_search_whole_levels_on_a_star():
+    # centre 0, leaves 1..9; tau = 5: a leaf's ball is {leaf, 0} (the next
+    # level, 8 leaves, would overflow and is dropped as a whole)
+    src = np.zeros(9, np.int64)
+    dst = np.arange(1, 10)
+    off, adj = I.from_edges(10, src, dst)
+    got = O.local_search(off, adj, np.array([[1, 2], [0, 5], [3, 3]], np.int32), 5)
+    assert got.tolist() == [2, 1, 0]
+    # the centre's ball is {0} alone (its first level has 9 vertices)
+    assert O.local_search(off, adj, np.array([[0, 1]], np.int32), 9).tolist() == [1]
+    assert O.local_search(off, adj, np.array([[0, 1]], np.int32), 1).tolist() == [0xFFFF]
+
+
+def test_local_search_unbounded_is_exact():
+    """tau >= n: the balls are whole components, so the answer is the BFS
+    distance (SciPy), 0xFFFF between components."""
+    off, adj = I.erdos_renyi(300, 330, seed=4)
+    n = off.size - 1
+    rng = np.random.default_rng(0)
+    pairs = rng.integers(0, n, size=(400, 2)).astype(np.int32)
+    A = sp.csr_matrix((np.ones(adj.size), adj, off), shape=(n, n))
+    D = shortest_path(A, unweighted=True)
+    got = O.local_search(off, adj, pairs, n)
+    for (u, v), a in zip(pairs, got):
+        exp = 0xFFFF if np.isinf(D[u, v]) else int(D[u, v])
+        assert a == exp
