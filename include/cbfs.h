@@ -268,6 +268,23 @@ int cbfs_labels_rows(cbfs_labels_t L, const uint8_t** host_rows, int64_t* host_s
  */
 int cbfs_query_distance(cbfs_labels_t L, const int32_t* pairs, int64_t q, uint16_t* out, void* stream);
 
+/*
+ * Distance query with the bounded bidirectional search of Appendix B fused
+ * in: for each pair, around u and around v a BFS ball on the resident graph
+ * g grows level by level, a level being kept only if the ball (its centre
+ * included) then holds at most tau vertices -- the first level that would
+ * overflow is dropped whole and that side stops.  The local answer is the
+ * minimum over vertices x in both balls of hops(u, x) + hops(x, v) (it is
+ * delta(u, v) whenever the balls meet); out[t] = min(local answer, label
+ * answer of cbfs_query_distance).  L may be NULL (local search only; no
+ * meeting gives 0xFFFF); otherwise its n must be g's.  1 <= tau <= 2048.
+ * One CTA per pair with up to 144 KB of shared memory.  Out-of-range ids
+ * give 0xFFFF and set the status word of L (or of g when L is NULL).
+ * Stream-ordered (asynchronous).
+ */
+int cbfs_query_local(cbfs_labels_t L, cbfs_graph_t g, const int32_t* pairs, int64_t q, int tau, uint16_t* out,
+                     void* stream);
+
 /* Synchronises `stream` and returns (then clears) the label store's device
  * status word: CBFS_OK or CBFS_E_INVALID after an out-of-range query id. */
 int cbfs_labels_status(cbfs_labels_t L, void* stream);

@@ -74,6 +74,7 @@ SIGNATURES = {
     "cbfs_labels_count": (_I, [_P, _P]),
     "cbfs_labels_rows": (_I, [_P, _P, _P]),
     "cbfs_query_distance": (_I, [_P, _P, _I64, _P, _P]),
+    "cbfs_query_local": (_I, [_P, _P, _P, _I64, _I, _P, _P]),
     "cbfs_labels_status": (_I, [_P, _P]),
     "cbfs_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -257,6 +258,20 @@ class Graph:
                                            ctypes.byref(t), _stream_ptr(stream))
         _check(rc, "cbfs_run_batched_labels")
         return dist, masks
+
+    def query_local(self, pairs: torch.Tensor, tau: int, labels: "Labels | None" = None,
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """``cbfs_query_local``: the bounded bidirectional search of Appendix B
+        (balls of at most ``tau`` vertices, whole BFS levels) fused with the
+        label query of ``labels`` when given.  pairs: CUDA int32 [q, 2];
+        returns int16 [q] holding the uint16 answers."""
+        q = pairs.shape[0] if pairs.dim() == 2 else pairs.numel() // 2
+        if out is None:
+            out = torch.empty(q, dtype=torch.int16, device=pairs.device)
+        rc = lib().cbfs_query_local(labels._h if labels is not None else None, self._h, _ptr(pairs) if q else None,
+                                    int(q), int(tau), _ptr(out) if q else None, _stream_ptr(stream))
+        _check(rc, "cbfs_query_local")
+        return out
 
     def profile(self, enable: bool) -> dict:
         """Reads and resets the kernel accounting (``cbfs_profile``); ``enable``

@@ -1247,6 +1247,26 @@ int slots_for(const cbfs_tune_t* tune, int C) {
     return p2;
 }
 
+}  // namespace
+
+namespace cbfs {
+
+int graph_view(const cbfs_graph_s* g, GraphView* out) {
+    if (!g || !out) return CBFS_E_INVALID;
+    out->n = g->n;
+    out->off = g->off_r;
+    out->adj = g->adj_r;
+    out->iperm = g->iperm_d;
+    out->device = g->device;
+    return CBFS_OK;
+}
+
+int* graph_status(cbfs_graph_s* g) { return g->status; }
+
+}  // namespace cbfs
+
+namespace {
+
 // Forgets every captured graph of the handle (and the call shapes seen once).
 void drop_graphs(cbfs_graph_s* g) {
     if (!g->graphs.empty()) cudaDeviceSynchronize();  // a replay may still be in flight

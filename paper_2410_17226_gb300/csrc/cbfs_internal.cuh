@@ -168,6 +168,18 @@ cudaError_t relabel_adjacency(int64_t n, int64_t n_big, int64_t n_mid, int64_t n
                               const int32_t* d_iperm, const int64_t* d_off, const int32_t* d_adj, const int64_t* d_off_r,
                               int32_t* d_adj_r, int sms, cudaStream_t st);
 
+// Read-only view of a resident graph's relabelled CSR (cbfs_core.cu), for
+// kernels outside the traversal (the local search of queries).
+struct GraphView {
+    int64_t n;
+    const int64_t* off;   // relabelled offsets [n + 1]
+    const int32_t* adj;   // relabelled adjacency (ranks)
+    const int32_t* iperm; // caller's id -> rank
+    int device;
+};
+int graph_view(const cbfs_graph_s* g, GraphView* out);
+int* graph_status(cbfs_graph_s* g);  // the handle's device status word
+
 // Label store (cbfs_labels.cu) fed by a batched run: reserve C rows' worth of
 // clusters at the store's count (uploads their ALL words), write nc clusters
 // of cluster-major outputs at position pos, or undo a reservation.

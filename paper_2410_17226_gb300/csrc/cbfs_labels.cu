@@ -127,6 +127,40 @@ __device__ __forceinline__ int best_offset_any(const uint64_t* su, const uint64_
     return -1;
 }
 
+// Minimum over the stored clusters of Delta_u + Delta_v + (smallest i + j with
+// S_u[i] & S_v[j] != 0), reduced over the calling warp (lanes stride over
+// clusters); 0x7fffffff when no cluster reaches both.
+template <int D, class T>
+__device__ __forceinline__ int label_min(int d, int C, int64_t P, int64_t block, const uint8_t* ru, const uint8_t* rv,
+                                         const uint64_t* alls, int lane) {
+    constexpr int DM = (D > 0 ? D : 15) + 1;
+    int best = 0x7fffffff;
+    for (int c = lane; c < C; c += 32) {
+        const int du = ru[c], dv = rv[c];
+        if (du == 0xFF || dv == 0xFF) continue;
+        uint64_t su[DM], sv[DM];
+        uint64_t ou = 0, ov = 0;
+        const int dd = D > 0 ? D : d;
+#pragma unroll
+        for (int i = 0; i < DM - 1; ++i) {
+            if (i < dd) {
+                su[i] = (uint64_t)__ldg(reinterpret_cast<const T*>(ru + P + i * block) + c);
+                sv[i] = (uint64_t)__ldg(reinterpret_cast<const T*>(rv + P + i * block) + c);
+                ou |= su[i];
+                ov |= sv[i];
+            }
+        }
+        const uint64_t all = __ldg(alls + c);
+        su[dd] = all & ~ou;
+        sv[dd] = all & ~ov;
+        const int off = D > 0 ? best_offset_fixed<D>(su, sv) : best_offset_any(su, sv, dd);
+        if (off >= 0) best = min(best, du + dv + off);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    return best;
+}
+
 template <int D, class T>
 __global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int64_t P, int64_t block, int64_t stride,
                                                const uint8_t* rows, const uint64_t* alls, const int32_t* pairs,
@@ -134,7 +168,6 @@ __global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int64_t 
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    constexpr int DM = (D > 0 ? D : 15) + 1;
     for (int64_t t = warp; t < q; t += nwarps) {
         const int32_t u = pairs[2 * t], v = pairs[2 * t + 1];
         if (u < 0 || v < 0 || (int64_t)u >= n || (int64_t)v >= n) {
@@ -148,33 +181,178 @@ __global__ void __launch_bounds__(256) k_query(int64_t n, int d, int C, int64_t 
             if (lane == 0) out[t] = 0;
             continue;
         }
-        const uint8_t* ru = rows + (int64_t)u * stride;
-        const uint8_t* rv = rows + (int64_t)v * stride;
-        int best = 0x7fffffff;
-        for (int c = lane; c < C; c += 32) {
-            const int du = ru[c], dv = rv[c];
-            if (du == 0xFF || dv == 0xFF) continue;
-            uint64_t su[DM], sv[DM];
-            uint64_t ou = 0, ov = 0;
-            const int dd = D > 0 ? D : d;
-#pragma unroll
-            for (int i = 0; i < DM - 1; ++i) {
-                if (i < dd) {
-                    su[i] = (uint64_t)__ldg(reinterpret_cast<const T*>(ru + P + i * block) + c);
-                    sv[i] = (uint64_t)__ldg(reinterpret_cast<const T*>(rv + P + i * block) + c);
-                    ou |= su[i];
-                    ov |= sv[i];
+        const int best = label_min<D, T>(d, C, P, block, rows + (int64_t)u * stride, rows + (int64_t)v * stride, alls,
+                                         lane);
+        if (lane == 0) out[t] = best == 0x7fffffff ? (uint16_t)0xFFFF : (uint16_t)min(best, 0xFFFE);
+    }
+}
+
+// ------------------------------------------------ bounded bidirectional search
+//
+// Appendix B: before answering from the labels, a query searches a few
+// vertices around both ends and takes the best meeting point.  Each side
+// grows a BFS ball level by level and keeps a level only if the ball then
+// holds at most tau vertices (a level that would overflow is dropped whole
+// and the side stops), so the balls do not depend on the order in which a
+// level's vertices are found.  The local answer is min over x in both balls
+// of hops(u, x) + hops(v, x); the query returns the smaller of that and the
+// label answer.  One CTA per pair; the two balls share one open-addressing
+// table in shared memory: key = vertex rank, hop word = hops from u (bits
+// 0-15) and from v (bits 16-31), 0xFFFF = not in that ball.
+
+constexpr int kLocalThreads = 256;
+constexpr int kMaxTau = 2048;  // the largest search size of Appendix B; 144 KB of shared memory
+constexpr uint32_t kNoHop = 0xFFFFu;
+
+struct LocalShared {
+    int32_t* key;
+    uint32_t* hop;
+    int32_t* list[2];
+    int hs_bits;
+};
+
+__device__ __forceinline__ uint32_t local_slot(int32_t x, int bits) {
+    return ((uint32_t)x * 0x9E3779B1u) >> (32 - bits);
+}
+
+// Adds x to side `side`'s ball at hop h; true when x was not in that ball.
+__device__ __forceinline__ bool local_insert(const LocalShared& sh, int32_t x, int side, uint32_t h) {
+    const uint32_t mask = (1u << sh.hs_bits) - 1u;
+    uint32_t s = local_slot(x, sh.hs_bits);
+    for (uint32_t probe = 0; probe <= mask; ++probe, s = (s + 1) & mask) {
+        int32_t k = sh.key[s];
+        if (k == -1) {
+            const int32_t prev = atomicCAS(&sh.key[s], -1, x);
+            k = prev == -1 ? x : prev;
+        }
+        if (k != x) continue;
+        const uint32_t shift = 16u * (uint32_t)side;
+        uint32_t old = sh.hop[s];
+        while (((old >> shift) & kNoHop) == kNoHop) {
+            const uint32_t want = (old & ~(kNoHop << shift)) | (h << shift);
+            const uint32_t got = atomicCAS(&sh.hop[s], old, want);
+            if (got == old) return true;
+            old = got;
+        }
+        return false;
+    }
+    return false;  // table full: cannot happen with the sizes below
+}
+
+// Grows one side's ball; returns its size (the list holds its vertices).
+__device__ int local_ball(const LocalShared& sh, const int64_t* off, const int32_t* adj, int32_t c, int side, int tau,
+                          int* s_cnt, int* s_over) {
+    int32_t* list = sh.list[side];
+    __syncthreads();  // every thread has read the previous ball's counters
+    if (threadIdx.x == 0) {
+        list[0] = c;
+        *s_cnt = 1;
+        *s_over = 0;
+        local_insert(sh, c, side, 0);
+    }
+    __syncthreads();
+    int lo = 0, size = 1;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = kLocalThreads / 32;
+    for (uint32_t h = 1; h < kNoHop; ++h) {  // at most tau levels
+        // one warp per frontier vertex, lanes over its arcs
+        for (int i = lo + wp; i < size; i += nw) {
+            const int32_t x = list[i];
+            const int64_t e1 = off[x + 1];
+            for (int64_t e = off[x] + lane; e < e1; e += 32) {
+                if (*(volatile int*)s_over) break;
+                const int32_t y = adj[e];
+                if (local_insert(sh, y, side, h)) {
+                    const int at = atomicAdd(s_cnt, 1);
+                    if (at < tau) list[at] = y;
+                    else *(volatile int*)s_over = 1;
                 }
             }
-            const uint64_t all = __ldg(alls + c);
-            su[dd] = all & ~ou;
-            sv[dd] = all & ~ov;
-            const int off = D > 0 ? best_offset_fixed<D>(su, sv) : best_offset_any(su, sv, dd);
-            if (off >= 0) best = min(best, du + dv + off);
+        }
+        __syncthreads();
+        const int grown = *s_cnt, over = *s_over;
+        if (over) {
+            // drop the partial level h everywhere in the table
+            const uint32_t shift = 16u * (uint32_t)side;
+            for (int s = threadIdx.x; s < (1 << sh.hs_bits); s += kLocalThreads)
+                if (((sh.hop[s] >> shift) & kNoHop) == h) atomicOr(&sh.hop[s], kNoHop << shift);
+            __syncthreads();
+            return size;
+        }
+        if (grown == size) return size;
+        lo = size;
+        size = grown;
+        __syncthreads();
+    }
+    return size;
+}
+
+template <int D, class T>
+__global__ void __launch_bounds__(kLocalThreads) k_query_local(int64_t n, int d, int C, int64_t P, int64_t block,
+                                                               int64_t stride, const uint8_t* rows,
+                                                               const uint64_t* alls, GraphView gv,
+                                                               const int32_t* pairs, int64_t q, int tau,
+                                                               int hs_bits, uint16_t* out, int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    LocalShared sh;
+    sh.hs_bits = hs_bits;
+    const int hs = 1 << hs_bits;
+    sh.key = reinterpret_cast<int32_t*>(smem);
+    sh.hop = reinterpret_cast<uint32_t*>(smem + 4 * (size_t)hs);
+    sh.list[0] = reinterpret_cast<int32_t*>(smem + 8 * (size_t)hs);
+    sh.list[1] = sh.list[0] + tau;
+    __shared__ int s_cnt, s_over, s_best, s_lab;
+    const int lane = threadIdx.x & 31;
+    for (int64_t t = blockIdx.x; t < q; t += gridDim.x) {
+        const int32_t u = pairs[2 * t], v = pairs[2 * t + 1];
+        if (u < 0 || v < 0 || (int64_t)u >= n || (int64_t)v >= n) {
+            if (threadIdx.x == 0) {
+                out[t] = 0xFFFF;
+                atomicCAS(status, 0, CBFS_E_INVALID);
+            }
+            continue;
+        }
+        if (u == v) {
+            if (threadIdx.x == 0) out[t] = 0;
+            continue;
+        }
+        if (threadIdx.x < 32) {
+            const int lab = C > 0 ? label_min<D, T>(d, C, P, block, rows + (int64_t)u * stride,
+                                                    rows + (int64_t)v * stride, alls, lane)
+                                  : 0x7fffffff;
+            if (lane == 0) s_lab = lab;
+        }
+        for (int s = threadIdx.x; s < hs; s += kLocalThreads) {
+            sh.key[s] = -1;
+            sh.hop[s] = 0xFFFFFFFFu;
+        }
+        if (threadIdx.x == 0) s_best = 0x7fffffff;
+        __syncthreads();
+        const int32_t ru = gv.iperm[u], rv = gv.iperm[v];
+        local_ball(sh, gv.off, gv.adj, ru, 0, tau, &s_cnt, &s_over);
+        const int sv = local_ball(sh, gv.off, gv.adj, rv, 1, tau, &s_cnt, &s_over);
+        // best meeting point over v's ball
+        int best = 0x7fffffff;
+        const uint32_t mask = (uint32_t)hs - 1u;
+        for (int i = threadIdx.x; i < sv; i += kLocalThreads) {
+            const int32_t x = sh.list[1][i];
+            uint32_t s = local_slot(x, hs_bits);
+            for (uint32_t probe = 0; probe <= mask; ++probe, s = (s + 1) & mask) {
+                if (sh.key[s] != x) continue;
+                const uint32_t w = sh.hop[s];
+                const uint32_t a = w & kNoHop, b = w >> 16;
+                if (a != kNoHop && b != kNoHop) best = min(best, (int)(a + b));
+                break;
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-        if (lane == 0) out[t] = best == 0x7fffffff ? (uint16_t)0xFFFF : (uint16_t)min(best, 0xFFFE);
+        if (lane == 0 && best != 0x7fffffff) atomicMin(&s_best, best);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int r = min(s_best, s_lab);
+            out[t] = r == 0x7fffffff ? (uint16_t)0xFFFF : (uint16_t)min(r, 0xFFFE);
+        }
+        __syncthreads();
     }
 }
 
@@ -203,6 +381,25 @@ void append_rows(const cbfs_labels_s* L, const uint8_t* dist, const uint64_t* ma
         }
 #undef CBFS_TILE
     }
+}
+
+template <int D, class T>
+cudaError_t launch_local(const cbfs_labels_s* L, const GraphView& gv, const int32_t* pairs, int64_t q, int tau,
+                         int hs_bits, uint16_t* out, int* status, cudaStream_t st) {
+    const size_t smem = 8 * ((size_t)1 << hs_bits) + 8 * (size_t)tau;
+    cudaError_t e = cudaFuncSetAttribute(k_query_local<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gv.device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_query_local<D, T>, kLocalThreads, smem);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(q, (int64_t)std::max(sms, 1) * std::max(occ, 1)));
+    if (L)
+        k_query_local<D, T><<<(unsigned)blocks, kLocalThreads, smem, st>>>(
+            L->n, L->d, L->count, L->P, L->block, L->stride, L->rows, L->alls, gv, pairs, q, tau, hs_bits, out, status);
+    else
+        k_query_local<D, T><<<(unsigned)blocks, kLocalThreads, smem, st>>>(gv.n, 0, 0, 0, 0, 0, nullptr, nullptr, gv,
+                                                                           pairs, q, tau, hs_bits, out, status);
+    return cudaGetLastError();
 }
 
 template <int D>
@@ -357,6 +554,44 @@ int cbfs_query_distance(cbfs_labels_t L, const int32_t* pairs, int64_t q, uint16
     }
     if (cudaGetLastError() != cudaSuccess) return CBFS_E_CUDA;
     return CBFS_OK;
+}
+
+int cbfs_query_local(cbfs_labels_t L, cbfs_graph_t g, const int32_t* pairs, int64_t q, int tau, uint16_t* out,
+                     void* stream) {
+    if (!g || q < 0 || (q > 0 && (!pairs || !out)) || tau < 1 || tau > kMaxTau) return CBFS_E_INVALID;
+    GraphView gv;
+    if (graph_view(g, &gv) != CBFS_OK) return CBFS_E_INVALID;
+    if (L && L->n != gv.n) return CBFS_E_INVALID;
+    if (q == 0) return CBFS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // both balls' entries plus the inserts racing past an overflow, at load <= 1/2
+    int hs_bits = 4;
+    while ((1 << hs_bits) < 2 * (2 * tau + 2 * kLocalThreads)) hs_bits++;
+    int* status = nullptr;
+    if (L) {
+        status = L->status;
+    } else {
+        status = graph_status(g);
+    }
+    cudaError_t e;
+    if (!L) {
+        e = launch_local<0, uint64_t>(nullptr, gv, pairs, q, tau, hs_bits, out, status, st);
+    } else {
+#define CBFS_LOCAL(DD)                                                                                    \
+    switch (L->wb) {                                                                                      \
+        case 1: e = launch_local<DD, uint8_t>(L, gv, pairs, q, tau, hs_bits, out, status, st); break;    \
+        case 2: e = launch_local<DD, uint16_t>(L, gv, pairs, q, tau, hs_bits, out, status, st); break;   \
+        case 4: e = launch_local<DD, uint32_t>(L, gv, pairs, q, tau, hs_bits, out, status, st); break;   \
+        default: e = launch_local<DD, uint64_t>(L, gv, pairs, q, tau, hs_bits, out, status, st); break;  \
+    }
+        switch (L->d) {
+            case 1: CBFS_LOCAL(1); break;
+            case 2: CBFS_LOCAL(2); break;
+            default: CBFS_LOCAL(0); break;
+        }
+#undef CBFS_LOCAL
+    }
+    return e == cudaSuccess ? CBFS_OK : CBFS_E_CUDA;
 }
 
 int cbfs_labels_status(cbfs_labels_t L, void* stream) {
