@@ -819,14 +819,22 @@ cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, in
 
 namespace {
 
-// Graph validation: ids in range, no self loop, strictly increasing lists,
-// every arc has its reverse (binary search in the neighbour's list).  One
-// thread, warp or CTA per vertex by degree class; flag = 1 on any failure.
-__device__ __forceinline__ bool arc_ok(int64_t n, const int64_t* off, const int32_t* adj, int64_t v, int64_t e,
-                                       int64_t o0) {
+// Graph check: ids in range, no self loop, lists strictly increasing (so no
+// repeated arc), and symmetry.  Symmetry is checked by counting: with a
+// strict order on vertices (the internal rank: higher degree first), every
+// arc v -> u whose head u comes after v must have its reverse, found by a
+// binary search in u's list -- the shorter one -- and those "forward" arcs
+// must be exactly half of all arcs.  (The forward arcs' reverses are
+// distinct backward arcs, so any backward arc without a forward partner
+// would make the backward ones outnumber the forward ones.)  One thread,
+// warp or CTA per vertex by degree class; flag = 1 on any failure.
+__device__ __forceinline__ bool arc_ok(int64_t n, const int64_t* off, const int32_t* adj, const int32_t* rank,
+                                       int64_t v, int64_t e, int64_t o0, unsigned long long& fwd) {
     const int32_t u = adj[e];
     if (u < 0 || (int64_t)u >= n || (int64_t)u == v) return false;
     if (e > o0 && adj[e - 1] >= u) return false;
+    if (rank[u] < rank[v]) return true;  // backward arc: counted from its partner
+    fwd += 1;
     int64_t lo = off[u], hi = off[u + 1];
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
@@ -836,13 +844,15 @@ __device__ __forceinline__ bool arc_ok(int64_t n, const int64_t* off, const int3
     return lo < off[u + 1] && (int64_t)adj[lo] == v;
 }
 
-__global__ void k_validate(int64_t n, const int64_t* off, const int32_t* adj, const int32_t* pl_small, int64_t n_small,
-                           const int32_t* pl_mid, int64_t n_mid, const int32_t* pl_big, int64_t n_big, int* flag) {
+__global__ void k_validate(int64_t n, const int64_t* off, const int32_t* adj, const int32_t* rank,
+                           const int32_t* pl_small, int64_t n_small, const int32_t* pl_mid, int64_t n_mid,
+                           const int32_t* pl_big, int64_t n_big, int* flag, unsigned long long* forward) {
     bool ok = true;
+    unsigned long long fwd = 0;
     for (int64_t i = blockIdx.x; i < n_big; i += gridDim.x) {
         const int64_t v = pl_big[i];
         const int64_t o0 = off[v], o1 = off[v + 1];
-        for (int64_t e = o0 + threadIdx.x; e < o1; e += blockDim.x) ok &= arc_ok(n, off, adj, v, e, o0);
+        for (int64_t e = o0 + threadIdx.x; e < o1; e += blockDim.x) ok &= arc_ok(n, off, adj, rank, v, e, o0, fwd);
     }
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -850,14 +860,17 @@ __global__ void k_validate(int64_t n, const int64_t* off, const int32_t* adj, co
     for (int64_t i = gw; i < n_mid; i += nwarps) {
         const int64_t v = pl_mid[i];
         const int64_t o0 = off[v], o1 = off[v + 1];
-        for (int64_t e = o0 + lane; e < o1; e += 32) ok &= arc_ok(n, off, adj, v, e, o0);
+        for (int64_t e = o0 + lane; e < o1; e += 32) ok &= arc_ok(n, off, adj, rank, v, e, o0, fwd);
     }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_small; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = pl_small[i];
         const int64_t o0 = off[v], o1 = off[v + 1];
-        for (int64_t e = o0; e < o1; ++e) ok &= arc_ok(n, off, adj, v, e, o0);
+        for (int64_t e = o0; e < o1; ++e) ok &= arc_ok(n, off, adj, rank, v, e, o0, fwd);
     }
     if (!ok) atomicExch(flag, 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fwd += __shfl_xor_sync(0xffffffffu, fwd, o);
+    if (lane == 0 && fwd) atomicAdd(forward, fwd);
 }
 
 // Work counters from outputs: per (cluster, vertex) the number of non-empty
@@ -1734,15 +1747,19 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
         // three degree classes are balanced separately (thread, warp, CTA per list)
         e = cudaMemsetAsync(g->status, 0, sizeof(int), st);
         if (e == cudaSuccess) {
-            k_validate<<<sms * 8, kThreads, 0, st>>>(n, g->off, g->adj, g->perm + g->n_big + g->n_mid, g->n_small,
-                                                     g->perm + g->n_big, g->n_mid, g->perm, g->n_big, g->status);
+            k_validate<<<sms * 8, kThreads, 0, st>>>(n, g->off, g->adj, g->iperm_d, g->perm + g->n_big + g->n_mid,
+                                                     g->n_small, g->perm + g->n_big, g->n_mid, g->perm, g->n_big,
+                                                     g->status, &d_stats->forward);
             e = cudaGetLastError();
         }
         int flag = 0;
+        unsigned long long forward = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, g->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&forward, &d_stats->forward, sizeof(forward), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return fail(CBFS_E_CUDA);
-        if (flag) return fail(CBFS_E_GRAPH);
+        if (flag || 2 * (int64_t)forward != nnz) return fail(CBFS_E_GRAPH);
     }
     if (e == cudaSuccess && nnz > 0)
         e = relabel_adjacency(n, g->n_big, g->n_mid, g->n_small, g->perm, g->iperm_d, g->off, g->adj, g->off_r, g->adj_r,

@@ -144,6 +144,7 @@ struct DegreeStats {
     unsigned long long big_pieces;             // kBigDeg-arc pieces of the lists longer than kBigDeg
     unsigned long long maxdeg;
     unsigned long long bad;                    // offsets not starting at 0, not ending at nnz, or decreasing
+    unsigned long long forward;                // graph check: arcs towards a later rank (half of all)
     unsigned long long order_bad;              // the rank order failed its check (never expected)
 };
 cudaError_t widen_offsets(const int32_t* in, int64_t* out, int64_t count, int sms, cudaStream_t st);

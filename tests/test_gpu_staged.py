@@ -205,3 +205,52 @@ def test_labels_and_host_outputs_with_rerun_waves(cb, slots):
     ref = valid_columns(rows_of(L3, n), C, C, d)
     assert (valid_columns(rows_of(L, n), C, C, d) == ref).all()
     assert (valid_columns(rows_of(L2, n), C, C, d) == ref).all()
+
+
+def _csr(n, arcs):
+    arcs = sorted(arcs)
+    off = np.zeros(n + 1, np.int64)
+    for a, _ in arcs:
+        off[a + 1] += 1
+    return np.cumsum(off), np.array([b for _, b in arcs], np.int32)
+
+
+def test_graph_check_by_counting(cb):
+    """Symmetry is checked by searching the reverse of every arc that points
+    to a later vertex of the degree order and by counting those arcs: a
+    missing reverse on either side must fail, symmetric graphs must pass."""
+    star = [(0, v) for v in range(1, 6)] + [(v, 0) for v in range(1, 6)]
+    off, adj = _csr(7, star)
+    cb.Graph(off, adj, validate=True).close()
+    # hub -> isolated vertex without its reverse: found missing by the search
+    off, adj = _csr(7, star + [(0, 6)])
+    with pytest.raises(cb.CbfsError) as e:
+        cb.Graph(off, adj, validate=True)
+    assert e.value.code == cb.E_GRAPH
+    # low-degree vertex -> hub without its reverse: only the count sees it
+    off, adj = _csr(7, star + [(6, 0)])
+    with pytest.raises(cb.CbfsError) as e:
+        cb.Graph(off, adj, validate=True)
+    assert e.value.code == cb.E_GRAPH
+    # two equal-degree vertices joined one way only (ties broken by id, both directions)
+    for a, b in ((3, 4), (4, 3)):
+        off, adj = _csr(7, star + [(a, b)])
+        with pytest.raises(cb.CbfsError) as e:
+            cb.Graph(off, adj, validate=True)
+        assert e.value.code == cb.E_GRAPH
+    # an extra symmetric edge keeps it valid; random symmetric graphs pass
+    off, adj = _csr(7, star + [(3, 4), (4, 3)])
+    cb.Graph(off, adj, validate=True).close()
+    for seed in range(3):
+        off, adj = I.erdos_renyi(500, 1500, seed=seed)
+        cb.Graph(off, adj, validate=True).close()
+    # an arc swapped for another endpoint keeps every degree but breaks symmetry
+    off, adj = I.rmat(10, seed=1)
+    adj2 = adj.copy()
+    v = int(np.argmax(np.diff(off) == 1))  # a vertex of degree 1
+    u = int(adj2[off[v]])
+    w = next(x for x in range(off.size - 1) if x not in (v, u) and x not in set(adj[off[v]:off[v + 1]]))
+    adj2[off[v]] = w
+    with pytest.raises(cb.CbfsError) as e:
+        cb.Graph(off, adj2, validate=True)
+    assert e.value.code == cb.E_GRAPH
