@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--fixed-tune", default="", help="'alpha,slots' instead of the autotuner (profiling runs)")
     ap.add_argument("--no-next", dest="next_rows", action="store_false",
                     help="skip the single-source BFS comparison and the d sweep")
+    ap.add_argument("--record-traffic", default="",
+                    help="ncu CSV (dram__bytes_read/write.sum of the traversal kernels of `runcli --host-loop`) "
+                         "to turn into profiles/traffic.json for the current kernel sources, then exit")
+    ap.add_argument("--traffic-clusters", type=int, default=16, help="clusters of the captured run")
     return ap.parse_args()
 
 
@@ -737,8 +741,47 @@ def run_cbfs(args, ws, rank, local):
     return 0
 
 
+def record_traffic(csv_path: str, clusters: int, note: str):
+    """DRAM bytes per cluster of the traversal kernels, from an ncu CSV of
+    one host-driven `runcli` call, scaled to the bench's 256-cluster launch
+    (traffic grows with the clusters at a fixed graph)."""
+    import csv as csv_
+
+    kinds = ("k_seed", "k_phase_a", "k_phase_b", "k_emit", "k_check_sources", "k_map_seeds")
+    total = 0.0
+    per_kernel = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv_.reader(f)]
+    hdr = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
+    cols = rows[hdr]
+    for r in rows[hdr + 1:]:
+        if len(r) != len(cols):
+            continue
+        rec = dict(zip(cols, r))
+        name = rec["Kernel Name"]
+        if not rec["Metric Name"].startswith("dram__bytes") or not any(k in name for k in kinds):
+            continue
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[rec["Metric Unit"]]
+        v = float(rec["Metric Value"].replace(",", "")) * scale
+        key = name.split("(")[0].replace("void ", "")
+        per_kernel[key] = per_kernel.get(key, 0.0) + v
+        total += v
+    per_cluster = total / clusters
+    out = {"traversal": {"dram_bytes_per_launch": int(per_cluster * 256), "per_cluster_bytes": int(per_cluster),
+                         "per_kernel_bytes": {k: int(v) for k, v in sorted(per_kernel.items())},
+                         "source_hash": kernel_source_hash(), "measured_on": note}}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
+    if args.record_traffic:
+        return record_traffic(args.record_traffic, args.traffic_clusters,
+                              f"R-MAT scale {args.scale}, {args.traffic_clusters} star clusters, host-driven "
+                              f"rounds; scaled to the 256-cluster launch by cluster count")
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)

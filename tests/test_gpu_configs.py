@@ -175,3 +175,34 @@ def test_config5_serving_scale22_labels(cb):
     L2.append(torch.from_numpy(od).cuda(), torch.from_numpy(om.view(np.int64)).cuda(), [len(S) for S in two])
     got = cb.as_numpy_u16(L2.query(torch.from_numpy(sample).cuda()))
     assert (got == O.query(od, om, [len(S) for S in two], sample)).all()
+
+
+def test_config2_host_outputs_and_labels_at_full_size(cb):
+    """Scale-22 R-MAT: 40 clusters (a full label group of 32 and a ragged one)
+    written to pinned host memory and to a label store by one
+    cbfs_run_batched_labels call; sampled clusters equal the oracle and the
+    label rows hold the same bytes as the host outputs."""
+    off, adj = I.rmat(22)
+    clusters, d = I.star_clusters(off, adj, 40, seed=I.MASTER_SEED + 5, size="uniform")
+    g = cb.Graph(off, adj)
+    n, C = g.n, len(clusters)
+    hd = torch.empty((C, n), dtype=torch.uint8).pin_memory()
+    hm = torch.empty((C, d, n), dtype=torch.int64).pin_memory()
+    L = cb.Labels(n, C, d)
+    g.run_batched_labels(clusters, d, L, dist=hd, masks=hm, tune={"slots": 4})
+    for c in (0, 31, 39):
+        od, om = O.cbfs_alg1(off, adj, clusters[c], d)
+        assert (hd[c].numpy() == od).all() and (hm[c].numpy().view(np.uint64) == om).all()
+    ptr, stride = L.rows()
+    rng = np.random.default_rng(1)
+    vs = rng.integers(0, n, 2000)
+
+    class _Rows:
+        __cuda_array_interface__ = {"shape": (n, stride), "typestr": "|u1", "data": (ptr, False), "version": 3}
+
+    rows = torch.as_tensor(_Rows(), device="cuda")[torch.from_numpy(vs).cuda()].cpu().numpy()
+    P = (C + 7) // 8 * 8
+    assert (rows[:, :C] == hd.numpy()[:, vs].T).all()
+    for s in range(d):
+        words = rows[:, P + 8 * s * C:P + 8 * (s + 1) * C].copy().view(np.uint64)
+        assert (words == hm.numpy()[:, s, vs].T.view(np.uint64)).all()
