@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--serve-s", type=float, default=2.0, help="seconds per offered serving load (0: skip)")
     ap.add_argument("--no-single-compare", dest="single_compare", action="store_false",
                     help="skip timing the clusters one call each")
-    ap.add_argument("--fixed-tune", default="", help="'alpha,slots' instead of the autotuner (profiling runs)")
+    ap.add_argument("--fixed-tune", default="", help="'alpha,slots[,small_deg,mid_deg]' instead of the autotuner (profiling runs)")
     ap.add_argument("--no-next", dest="next_rows", action="store_false",
                     help="skip the single-source BFS comparison and the d sweep")
     ap.add_argument("--record-traffic", default="",
@@ -499,11 +499,13 @@ def run_cbfs(args, ws, rank, local):
     n = off.size - 1
     g = cbfs.Graph(off, adj, validate=True)
     if args.fixed_tune:
-        a_, s_ = args.fixed_tune.split(",")
-        tn = {"pull_alpha": float(a_), "slots": int(s_), "cached": None}
+        parts = args.fixed_tune.split(",")
+        tn = {"pull_alpha": float(parts[0]), "slots": int(parts[1]), "cached": None,
+              "small_deg": int(parts[2]) if len(parts) > 2 else 0, "mid_deg": int(parts[3]) if len(parts) > 3 else 0}
     else:
         tn = tune.autotune(g, clusters, d, key_extra=f"rmat-s{args.scale}-{tune.signature(off)}")
-    tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"]}
+    tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"], "small_deg": tn.get("small_deg", 0),
+            "mid_deg": tn.get("mid_deg", 0)}
     dist = torch.empty((C, n), dtype=torch.uint8, device=dev)
     masks = torch.empty((C, d, n), dtype=torch.int64, device=dev)
     L = cbfs.Labels(n, C, d)

@@ -64,7 +64,7 @@ typedef struct cbfs_labels_s* cbfs_labels_t;
 typedef struct cbfs_tune_s {
     /* Direction optimisation (Appendix A, EdgeMap): a round runs dense (pull)
        when |F| + sum_{u in F} deg(u) > pull_alpha * nnz * (clusters in flight);
-       < 0 disables pull.  0 = default (0.02; the paper's commented rule is 1/10). */
+       < 0 disables pull.  0 = default (0.08; the paper's commented rule is 1/10). */
     float pull_alpha;
     /* clusters traversed concurrently in one batched wave; rounded down to a
        power of two in 1..8.  0 = default (4). */
@@ -77,7 +77,13 @@ typedef struct cbfs_tune_s {
        whose rounds loop on the device (conditional WHILE nodes).  Calls with
        kernel timing enabled (cbfs_profile) always use the host loop. */
     int host_loop;
-    int reserved[4];
+    /* degree classes of the dense edge phase: one thread per vertex of degree
+       <= small_deg (1..32), one warp per vertex of degree <= mid_deg
+       (small_deg..65536), one CTA per 2048-arc piece above.  0 = defaults
+       (32, 16384); the autotuner picks them per graph. */
+    int small_deg;
+    int mid_deg;
+    int reserved[2];
 } cbfs_tune_t;
 
 /* Work counters of one cluster's traversal (Theorem 1). */

@@ -37,7 +37,8 @@ class CbfsError(RuntimeError):
 
 class Tune(ctypes.Structure):
     _fields_ = [("pull_alpha", ctypes.c_float), ("slots", ctypes.c_int), ("dense_div", ctypes.c_int),
-                ("host_loop", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("host_loop", ctypes.c_int), ("small_deg", ctypes.c_int), ("mid_deg", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class KernelTimes(ctypes.Structure):
@@ -216,6 +217,8 @@ class Graph:
             t.slots = int(tune.get("slots", 0))
             t.dense_div = int(tune.get("dense_div", 0))
             t.host_loop = int(tune.get("host_loop", 0))
+            t.small_deg = int(tune.get("small_deg", 0))
+            t.mid_deg = int(tune.get("mid_deg", 0))
         return t
 
     def run_batched(self, clusters: Sequence | None, d: int, dist: torch.Tensor | None = None,

@@ -935,8 +935,19 @@ struct cbfs_graph_s {
     int64_t masks_r_cap = 0;
     int32_t* pl = nullptr;  // pull lists: small | mid | big
     uint64_t* pull_pieces = nullptr;  // (rank << 32 | piece) of every vertex of degree > kPullMid
-    int64_t n_small = 0, n_mid = 0, n_big = 0;
+    int64_t n_small = 0, n_mid = 0, n_big = 0;  // degree classes of the default thresholds
     int64_t big_vertices = 0, big_pieces = 0;
+    // pull classes for the thresholds of the current call (cbfs_tune_t small_deg, mid_deg):
+    // pl holds them; hub piece lists are kept per mid threshold
+    std::vector<unsigned long long> deg_count;  // vertices of degree 0..kMaxMidDeg, then above
+    int cls_small = 0, cls_mid = 0;
+    int64_t c_small = 0, c_mid = 0, c_big = 0;
+    struct HubPieces {
+        int mid;
+        uint64_t* d;  // owned, except the create-time list (== pull_pieces)
+        int64_t count;
+    };
+    std::vector<HubPieces> pieces;
     int grid_p[4] = {0, 0, 0, 0};  // phase-kernel grid for P = 1, 2, 4, 8 (SMs x resident CTAs)
     int device = 0;
     // scratch, sized for cap_slots clusters in flight
@@ -1288,6 +1299,67 @@ void drop_graphs(cbfs_graph_s* g) {
     g->seen.clear();
 }
 
+// Pull classes for thresholds (small, mid): class sizes from the degree
+// histogram (ranks are sorted by degree, so each class is a rank range), the
+// rank lists rebuilt on the stream, the hub pieces (kBigDeg arcs each, in
+// piece-major order) built once per mid threshold.
+int ensure_classes(cbfs_graph_s* g, int small, int mid, cudaStream_t st) {
+    if (small == g->cls_small && mid == g->cls_mid) return CBFS_OK;
+    const auto& h = g->deg_count;
+    unsigned long long total = 0, le_small = 0, le_mid = 0;
+    for (int dg = 1; dg < (int)h.size(); ++dg) {
+        total += h[dg];
+        if (dg <= small) le_small += h[dg];
+        if (dg <= mid) le_mid += h[dg];
+    }
+    const int64_t c_small = (int64_t)le_small, c_mid = (int64_t)(le_mid - le_small), c_big = (int64_t)(total - le_mid);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+    CK(class_lists(g->pl, c_small, c_mid, c_big, std::max(sms, 1), st));
+    bool have = false;
+    for (const auto& hp : g->pieces) have |= (hp.mid == mid);
+    if (!have) {
+        std::vector<int64_t> hub_off((size_t)c_big + 1, 0);
+        if (c_big > 0) {
+            CK(cudaMemcpyAsync(hub_off.data(), g->off_r, sizeof(int64_t) * hub_off.size(), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        std::vector<uint64_t> pcs;
+        for (int64_t k = 0;; ++k) {
+            bool any = false;
+            for (int64_t r = 0; r < c_big; ++r) {
+                if (k * kBigDeg >= hub_off[(size_t)r + 1] - hub_off[(size_t)r]) break;  // degrees do not increase
+                pcs.push_back(((uint64_t)r << 32) | (uint64_t)k);
+                any = true;
+            }
+            if (!any) break;
+        }
+        cbfs_graph_s::HubPieces hp{mid, nullptr, (int64_t)pcs.size()};
+        int rc = dev_alloc(&hp.d, hp.count);
+        if (rc) return rc;
+        if (!pcs.empty()) {
+            CK(cudaMemcpyAsync(hp.d, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));  // pcs dies with this scope
+        }
+        if (g->pieces.size() >= 8) {  // keep the create-time list, drop the oldest other one
+            for (size_t i = 0; i < g->pieces.size(); ++i) {
+                if (g->pieces[i].d == g->pull_pieces) continue;
+                drop_graphs(g);  // captured graphs may hold its address
+                dev_free(g->pieces[i].d);
+                g->pieces.erase(g->pieces.begin() + (long)i);
+                break;
+            }
+        }
+        g->pieces.push_back(hp);
+    }
+    g->cls_small = small;
+    g->cls_mid = mid;
+    g->c_small = c_small;
+    g->c_mid = c_mid;
+    g->c_big = c_big;
+    return CBFS_OK;
+}
+
 // True when p is host memory (pinned or pageable): kernels do not write it.
 bool is_host_pointer(const void* p) {
     cudaPointerAttributes a;
@@ -1323,10 +1395,16 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                        uint64_t* masks, cbfs_labels_s* L, int lbase, const cbfs_tune_t* tune, cudaStream_t st) {
     int rc = CBFS_OK;
     const int P = slots_for(tune, C);
-    float alpha = 0.02f;
+    float alpha = 0.08f;
     if (tune && tune->pull_alpha != 0.f) alpha = tune->pull_alpha;
     int dense_div = 16;
     if (tune && tune->dense_div != 0) dense_div = tune->dense_div < 0 ? 0 : tune->dense_div;
+    const int small_deg = (tune && tune->small_deg) ? tune->small_deg : (int)kPullSmall;
+    const int mid_deg = (tune && tune->mid_deg) ? tune->mid_deg : kDefaultMidDeg;
+    if (small_deg < 1 || small_deg > (int)kPullSmall || mid_deg < small_deg || mid_deg > kMaxMidDeg)
+        return CBFS_E_INVALID;
+    rc = ensure_classes(g, small_deg, mid_deg, st);
+    if (rc) return rc;
     rc = ensure_scratch(g, P);
     if (!rc) rc = ensure_dev(&g->masks_r, &g->masks_r_cap, std::max<int64_t>(1, g->n * d * P));
     if (rc) return rc;
@@ -1440,13 +1518,16 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.piece_ent = g->piece_ent;
     w.piece_no = g->piece_no;
     w.pl_small = g->pl;
-    w.pl_mid = g->pl + g->n_small;
-    w.pl_big = g->pl + g->n_small + g->n_mid;
-    w.n_small = g->n_small;
-    w.n_mid = g->n_mid;
-    w.n_big = g->n_big;
-    w.pull_pieces = g->pull_pieces;
-    w.n_pull_pieces = g->big_pieces;
+    w.pl_mid = g->pl + g->c_small;
+    w.pl_big = g->pl + g->c_small + g->c_mid;
+    w.n_small = g->c_small;
+    w.n_mid = g->c_mid;
+    w.n_big = g->c_big;
+    for (const auto& hp : g->pieces) {
+        if (hp.mid != g->cls_mid) continue;
+        w.pull_pieces = hp.d;
+        w.n_pull_pieces = hp.count;
+    }
     w.status = g->status;
     w.alpha = alpha;
     w.dist_r = g->dist_r;
@@ -1689,7 +1770,7 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     if (!rc) rc = dev_alloc(&g->ctl, kMaxRounds);
     if (!rc) rc = dev_alloc(&g->status, 1);
     if (!rc) rc = dev_alloc(&d_stats, 1);
-    if (!rc) rc = dev_alloc(&scratch, rank_scratch_words(n));
+    if (!rc) rc = dev_alloc(&scratch, std::max<int64_t>(rank_scratch_words(n), kMaxMidDeg + 2));
     if (!rc) rc = dev_alloc(&g->perm, n);
     if (!rc) rc = dev_alloc(&g->iperm_d, n);
     if (!rc) rc = dev_alloc(&g->off_r, n + 1);
@@ -1765,6 +1846,12 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
         e = relabel_adjacency(n, g->n_big, g->n_mid, g->n_small, g->perm, g->iperm_d, g->off, g->adj, g->off_r, g->adj_r,
                               sms, st);
     if (e == cudaSuccess) e = class_lists(g->pl, g->n_small, g->n_mid, g->n_big, sms, st);
+    // degree histogram: class sizes of other thresholds without another pass
+    g->deg_count.assign(kMaxMidDeg + 2, 0ull);
+    if (e == cudaSuccess) e = degree_hist(n, g->off, reinterpret_cast<unsigned long long*>(scratch), sms, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->deg_count.data(), scratch, sizeof(unsigned long long) * g->deg_count.size(),
+                            cudaMemcpyDeviceToHost, st);
     // pieces of the high-degree lists for the dense edge phase (ranks [0, n_big)),
     // piece-major (every hub's first piece before any second piece): a later
     // piece usually finds its hub already complete and skips
@@ -1793,6 +1880,12 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
         e = cudaMemcpyAsync(g->pull_pieces, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // pcs dies with this scope
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(CBFS_E_CUDA);
+    g->cls_small = (int)kPullSmall;
+    g->cls_mid = (int)kPullMid;
+    g->c_small = g->n_small;
+    g->c_mid = g->n_mid;
+    g->c_big = g->n_big;
+    g->pieces.push_back({(int)kPullMid, g->pull_pieces, g->big_pieces});
     dev_free(scratch);
     dev_free(d_stats);
     dev_free(g->adj);  // the caller's adjacency is no longer needed
@@ -1811,6 +1904,8 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->adj_r);
     dev_free(g->perm);
     dev_free(g->iperm_d);
+    for (auto& hp : g->pieces)
+        if (hp.d != g->pull_pieces) dev_free(hp.d);
     dev_free(g->pull_pieces);
     dev_free(g->masks_r);
     dev_free(g->pl);

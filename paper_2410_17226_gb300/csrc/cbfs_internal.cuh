@@ -18,6 +18,10 @@ constexpr int kMaxRounds = 288;     // > 254 + 15 + 1: Delta < 255, offsets <= 1
 constexpr int64_t kBigDeg = 2048;   // push: longer lists are cut into pieces of this size
 constexpr int64_t kPullSmall = 32;  // pull: thread per vertex up to this degree
 constexpr int64_t kPullMid = 2048;  // pull: warp per vertex up to this degree, CTA above
+                                    // (both are defaults: a call may set its own, see cbfs_tune_t)
+constexpr int kMaxMidDeg = 65536;   // largest warp-per-vertex threshold a call may ask for
+constexpr int kDefaultMidDeg = 16384;  // a call's default: warps beat 2048-arc CTA pieces up to
+                                       // about this degree on power-law graphs (measured)
 constexpr int kTileMin = kThreads;  // smallest phase-A tile (P >= 4)
 constexpr int kTileMax = 4 * kThreads;
 
@@ -159,6 +163,8 @@ cudaError_t rank_order_device(int64_t n, const int64_t* off, uint64_t maxdeg, in
 // Exclusive scan of count int64 values into out[0..count] (out[count] = total);
 // in == out is allowed.  sums: tile sums, (count + 4095) / 4096 entries.
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, int64_t* sums, cudaStream_t st);
+// Vertices of each degree 0..kMaxMidDeg, and above it in hist[kMaxMidDeg + 1].
+cudaError_t degree_hist(int64_t n, const int64_t* off, unsigned long long* hist, int sms, cudaStream_t st);
 // Pull lists in rank space: small | mid | big.
 cudaError_t class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big, int sms, cudaStream_t st);
 // Seeds hold callers' ids in their low 32 bits: rewrite them as ranks.

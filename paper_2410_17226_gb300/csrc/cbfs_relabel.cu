@@ -346,6 +346,25 @@ __global__ void k_check_rank(int64_t n, const int32_t* perm, const int32_t* iper
     if (bad) atomicExch(&st->order_bad, 1ull);
 }
 
+// Degree histogram for the pull classes of any threshold pair: the common
+// low degrees are counted per CTA in shared memory and merged with one atomic
+// per non-empty bin; the rare higher ones go to the global bins directly.
+constexpr int kHistShared = 4096;
+
+__global__ void __launch_bounds__(kThreads) k_degree_hist(int64_t n, const int64_t* off, unsigned long long* hist) {
+    __shared__ unsigned int bins[kHistShared + 1];
+    for (int i = threadIdx.x; i <= kHistShared; i += kThreads) bins[i] = 0;
+    __syncthreads();
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t dg = off[v + 1] - off[v];
+        if (dg <= kHistShared) atomicAdd(&bins[(int)dg], 1u);
+        else atomicAdd(&hist[dg > kMaxMidDeg ? kMaxMidDeg + 1 : (int)dg], 1ull);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= kHistShared; i += kThreads)
+        if (bins[i]) atomicAdd(&hist[i], (unsigned long long)bins[i]);
+}
+
 // Pull lists in rank space, in the order small | mid | big: the degree
 // classes are consecutive rank ranges (big first).
 __global__ void k_class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big) {
@@ -455,6 +474,15 @@ cudaError_t rank_order_device(int64_t n, const int64_t* off, uint64_t maxdeg, in
     e = exclusive_scan_i64(r.deg_r, n, off_r, r.sums, st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+cudaError_t degree_hist(int64_t n, const int64_t* off, unsigned long long* hist, int sms, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (kMaxMidDeg + 2), st);
+    if (e == cudaSuccess && n > 0) {
+        k_degree_hist<<<sms * 4, kThreads, 0, st>>>(n, off, hist);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big, int sms, cudaStream_t st) {

@@ -27,7 +27,9 @@ def main(argv=None) -> int:
     ap.add_argument("--scale", type=int, default=20, help="R-MAT scale, or the grid side for --graph grid")
     ap.add_argument("--clusters", type=int, default=16)
     ap.add_argument("--slots", type=int, default=8)
-    ap.add_argument("--pull-alpha", type=float, default=0.02)
+    ap.add_argument("--pull-alpha", type=float, default=0.0, help="0: the library default")
+    ap.add_argument("--small-deg", type=int, default=0, help="thread-per-vertex degree limit (0: default)")
+    ap.add_argument("--mid-deg", type=int, default=0, help="warp-per-vertex degree limit (0: default)")
     ap.add_argument("--host-loop", action="store_true", help="host-driven rounds instead of a CUDA graph")
     ap.add_argument("--repeat", type=int, default=0, help="extra calls after the first")
     args = ap.parse_args(argv)
@@ -43,7 +45,8 @@ def main(argv=None) -> int:
     C = len(clusters)
     dist = torch.empty((C, g.n), dtype=torch.uint8, device="cuda")
     masks = torch.empty((C, d, g.n), dtype=torch.int64, device="cuda")
-    tune = {"slots": args.slots, "pull_alpha": args.pull_alpha, "host_loop": int(args.host_loop)}
+    tune = {"slots": args.slots, "pull_alpha": args.pull_alpha, "host_loop": int(args.host_loop),
+            "small_deg": args.small_deg, "mid_deg": args.mid_deg}
     ms = 0.0
     for _ in range(1 + args.repeat):
         torch.cuda.synchronize()

@@ -64,7 +64,8 @@ def test_config2_scale22_256_clusters_batched(cb):
     clusters, d = I.star_clusters(off, adj, 256, seed=I.MASTER_SEED + 1, size="uniform")
     g = cb.Graph(off, adj)
     tn = tune.autotune(g, clusters, d, key_extra=f"rmat-s22-{tune.signature(off)}")
-    tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"]}
+    tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"], "small_deg": tn.get("small_deg", 0),
+            "mid_deg": tn.get("mid_deg", 0)}
     dist, masks = g.run_batched(clusters, d, tune=tset)
     assert_invariants(dist, masks, clusters)
     for c in (0, 131, 255):

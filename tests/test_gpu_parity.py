@@ -252,3 +252,42 @@ def test_graph_replay_after_the_seed_buffer_grows(cb):
         dd, dm = g.run_batched([S], 2)
         od, om = O.cbfs_alg1(off, adj, S, 2)
         assert (dd[0].cpu().numpy() == od).all() and (cb.as_numpy_u64(dm[0]) == om).all()
+
+
+@pytest.mark.parametrize("small,mid", [(1, 1), (8, 64), (32, 32), (16, 4096), (32, 2048), (4, 300), (32, 65536)])
+def test_pull_degree_classes_equal_oracle(cb, small, mid):
+    """Runtime degree classes of the dense edge phase (thread per vertex up to
+    `small`, warp up to `mid`, CTA pieces above): bit-exact for every pair,
+    including the degenerate ones, on a power-law graph, a hub graph and a
+    grid, switching classes between calls on one handle."""
+    leaves = 10000
+    src = np.concatenate([np.zeros(leaves, np.int64), np.arange(leaves, leaves + 40)])
+    dst = np.concatenate([np.arange(1, leaves + 1), np.arange(leaves + 1, leaves + 41)])
+    cases = [("rmat", I.rmat(14, seed=13)), ("hub", I.from_edges(leaves + 41, src, dst)), ("grid", I.road_grid(80, seed=3))]
+    for name, (off, adj) in cases:
+        g = cb.Graph(off, adj)
+        if name == "grid":
+            clusters, ds = I.ball_clusters(off, adj, 5, 12, seed=5)
+            d = max(ds)
+        else:
+            clusters, d = I.star_clusters(off, adj, 6, seed=small + mid, size="uniform")
+        for slots in (1, 4, 8):
+            for tune in ({"slots": slots, "pull_alpha": 1e-9, "small_deg": small, "mid_deg": mid},
+                         {"slots": slots, "small_deg": small, "mid_deg": mid, "host_loop": 1},
+                         {"slots": slots, "pull_alpha": 1e-9}):  # back to the defaults
+                for _ in range(2):
+                    dist, masks = g.run_batched(clusters, d, tune=tune)
+                for c, S in enumerate(clusters):
+                    od, om = O.cbfs_alg1(off, adj, S, d)
+                    assert (dist[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(masks[c]) == om).all(), \
+                        (name, small, mid, tune, c)
+
+
+def test_pull_degree_classes_reject_bad_thresholds(cb):
+    off, adj = I.rmat(10, seed=1)
+    g = cb.Graph(off, adj)
+    clusters, d = I.star_clusters(off, adj, 2, seed=1)
+    for small, mid in ((33, 64), (8, 4), (8, 65537), (-1, 64)):
+        with pytest.raises(cb.CbfsError) as e:
+            g.run_batched(clusters, d, tune={"small_deg": small, "mid_deg": mid})
+        assert e.value.code == cb.E_INVALID
