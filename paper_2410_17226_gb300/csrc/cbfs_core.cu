@@ -1395,7 +1395,11 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                        uint64_t* masks, cbfs_labels_s* L, int lbase, const cbfs_tune_t* tune, cudaStream_t st) {
     int rc = CBFS_OK;
     const int P = slots_for(tune, C);
-    float alpha = 0.08f;
+    // default switch: a single-source BFS pulls early (its pull stops at the
+    // first frontier neighbour); a cluster must collect every source bit
+    int max_k = 0;
+    for (int c = 0; c < C; ++c) max_k = std::max(max_k, coff[c + 1] - coff[c]);
+    float alpha = max_k == 1 ? 0.02f : 0.08f;
     if (tune && tune->pull_alpha != 0.f) alpha = tune->pull_alpha;
     int dense_div = 16;
     if (tune && tune->dense_div != 0) dense_div = tune->dense_div < 0 ? 0 : tune->dense_div;
