@@ -34,8 +34,9 @@ if ROOT not in sys.path:
 from paper_2410_17226_gb300 import inputs as I  # noqa: E402
 
 METRIC = "C-BFS source-edge GTEPS + HBM roofline fraction; label-query p50/p99 latency"
-WORKLOAD = ("batched C-BFS: undirected R-MAT scale 22 (edge factor 16, a=0.57 b=c=0.19, int32 CSR), "
-            "256 star clusters of 1-64 sources (seeded random centres + random neighbour subsets), d=2, "
+def workload_text(scale: int, clusters: int) -> str:
+    return (f"batched C-BFS: undirected R-MAT scale {scale} (edge factor 16, a=0.57 b=c=0.19, int32 CSR), "
+            f"{clusters} star clusters of 1-64 sources (seeded random centres + random neighbour subsets), d=2, "
             "autotuned push/pull; + label append + 65,536-pair query")
 ARC_BYTES = 13      # per arc scanned: 4 B neighbour id + 1 B Delta_v check + 8 B subset OR
 VERTEX_BYTES = 41   # per frontier appearance: 8 B offsets + 33 B vertex-phase reads/writes
@@ -453,9 +454,11 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall_total / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph": f"rmat-s{args.scale}-ef16", "clusters": args.clusters, "d": d},
+        "config": {"workload": workload_text(args.scale, args.clusters), "graph": f"rmat-s{args.scale}-ef16",
+                   "clusters": args.clusters, "d": d},
         "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                         "sample": "each step: 16 of the 256 clusters, Algorithm 1 in plain C, one cluster per core"},
+                         "sample": f"each step: 16 of the {len(clusters)} clusters, Algorithm 1 in plain C, "
+                                   "one cluster per core"},
         "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -557,7 +560,7 @@ def run_cbfs(args, ws, rank, local):
     cbfs_step_ms = cbfs_ms / args.steps
     achieved = alg_bytes_step / (cbfs_step_ms / 1e3) / 1e9
     traffic = ncu_traffic("traversal")
-    roofline = {"kernel": "cbfs_run_batched traversal graph (vertex + edge phases of all 256 clusters)",
+    roofline = {"kernel": f"cbfs_run_batched traversal graph (vertex + edge phases of all {C} clusters)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "avg_launch_ms": round(cbfs_step_ms, 3), "alg_bytes_per_launch": int(alg_bytes_step)}
@@ -718,7 +721,8 @@ def run_cbfs(args, ws, rank, local):
             "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "graph": f"rmat-s{args.scale}-ef16", "n": n, "nnz": int(adj.size),
+            "config": {"workload": workload_text(args.scale, C), "graph": f"rmat-s{args.scale}-ef16", "n": n,
+                       "nnz": int(adj.size),
                        "clusters": C, "sources": int(ks.sum()), "d": d, "tune": tset,
                        "tune_cached": tn.get("cached"), "query_batch": args.query_batch,
                        "l2": "inputs larger than L2 (0.5 GB CSR, 18 GB outputs, 18 GB labels)"},

@@ -64,9 +64,10 @@ typedef struct cbfs_labels_s* cbfs_labels_t;
 typedef struct cbfs_tune_s {
     /* Direction optimisation (Appendix A, EdgeMap): a round runs dense (pull)
        when |F| + sum_{u in F} deg(u) > pull_alpha * nnz * (clusters in flight);
-       < 0 disables pull.  0 = default: 0.02 when every cluster of the call is
-       a single source (a plain BFS, whose pull stops at the first frontier
-       neighbour), else 0.08 (the paper's commented rule is 1/10). */
+       < 0 disables pull.  0 = default, per wave: 0.02 when the wave's
+       clusters have at most 4 sources each (their pull stops after a few
+       frontier neighbours; a plain BFS is k = 1), else 0.08 (the paper's
+       commented rule is 1/10). */
     float pull_alpha;
     /* clusters traversed concurrently in one batched wave; rounded down to a
        power of two in 1..8.  0 = default (4). */

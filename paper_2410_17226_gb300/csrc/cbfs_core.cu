@@ -1395,12 +1395,18 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                        uint64_t* masks, cbfs_labels_s* L, int lbase, const cbfs_tune_t* tune, cudaStream_t st) {
     int rc = CBFS_OK;
     const int P = slots_for(tune, C);
-    // default switch: a single-source BFS pulls early (its pull stops at the
-    // first frontier neighbour); a cluster must collect every source bit
-    int max_k = 0;
-    for (int c = 0; c < C; ++c) max_k = std::max(max_k, coff[c + 1] - coff[c]);
-    float alpha = max_k == 1 ? 0.02f : 0.08f;
-    if (tune && tune->pull_alpha != 0.f) alpha = tune->pull_alpha;
+    // Default switch factor, per wave: a wave of small clusters (at most 4
+    // sources each) pulls early -- its pull stops after a few frontier
+    // neighbours -- while larger clusters must collect every source bit
+    // (measured: 0.02 vs 0.08 is 1.5x faster for k = 2..4, equal from k = 8).
+    const bool alpha_given = tune && tune->pull_alpha != 0.f;
+    const float alpha = alpha_given ? tune->pull_alpha : 0.08f;
+    auto wave_alpha = [&](int wv) -> float {
+        if (alpha_given) return alpha;
+        int max_k = 0;
+        for (int c = wv * P; c < std::min(C, (wv + 1) * P); ++c) max_k = std::max(max_k, coff[c + 1] - coff[c]);
+        return max_k <= 4 ? 0.02f : 0.08f;
+    };
     int dense_div = 16;
     if (tune && tune->dense_div != 0) dense_div = tune->dense_div < 0 ? 0 : tune->dense_div;
     const int small_deg = (tune && tune->small_deg) ? tune->small_deg : (int)kPullSmall;
@@ -1554,6 +1560,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         uint64_t key = 1469598103934665603ull;
         for (int wv = 0; wv < nwaves; ++wv) {
             waves[wv].nslots = std::min(P, C - wv * P);
+            waves[wv].alpha = wave_alpha(wv);
             waves[wv].slots = g->slots + (size_t)wv * P;
             key = fnv1a(key, &waves[wv], sizeof(Wave));
         }
@@ -1614,6 +1621,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     auto run_wave = [&](int wv, int bound, bool rerun, int* rounds_out) -> int {
         const int c0 = wv * P;
         w.nslots = std::min(P, C - c0);
+        w.alpha = wave_alpha(wv);
         w.slots = g->slots + (size_t)wv * P;
         CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
