@@ -601,8 +601,9 @@ def run_cbfs(args, ws, rank, local):
     # label-query latency: single requests of U{1..65536} pairs, H2D + kernel + D2H each
     lat = []
     rng = np.random.default_rng(rank_seed(rank) + 11)
-    pin_pairs = torch.from_numpy(pairs).pin_memory()
-    pin_ans = torch.empty(args.query_batch, dtype=torch.int16).pin_memory()
+    pin_pairs = cbfs.pinned_empty(pairs.shape, torch.int32)
+    pin_pairs.copy_(torch.from_numpy(pairs))
+    pin_ans = cbfs.pinned_empty(args.query_batch, torch.int16)
     qtot, t_q0 = 0, time.perf_counter()
     for _ in range(args.latency_requests):
         q = int(rng.integers(1, args.query_batch + 1))
@@ -678,10 +679,13 @@ def run_cbfs(args, ws, rank, local):
     # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        off_pin = torch.from_numpy(off).pin_memory()
-        adj_pin = torch.from_numpy(adj).pin_memory()
-        dist_h = torch.empty((C, n), dtype=torch.uint8).pin_memory()
-        masks_h = torch.empty((C, d, n), dtype=torch.int64).pin_memory()
+        # page-locked host buffers from the library (cudaHostAlloc)
+        off_pin = cbfs.pinned_empty(off.shape, torch.int64)
+        off_pin.copy_(torch.from_numpy(off))
+        adj_pin = cbfs.pinned_empty(adj.shape, torch.int32)
+        adj_pin.copy_(torch.from_numpy(adj))
+        dist_h = cbfs.pinned_empty((C, n), torch.uint8)
+        masks_h = cbfs.pinned_empty((C, d, n), torch.int64)
         bi = off.nbytes + adj.nbytes + src_cat.nbytes + coff.nbytes + pairs.nbytes
         bo = dist_h.numel() + masks_h.numel() * 8 + args.query_batch * 2
         del dist, masks

@@ -298,6 +298,17 @@ int cbfs_query_local(cbfs_labels_t L, cbfs_graph_t g, const int32_t* pairs, int6
  * status word: CBFS_OK or CBFS_E_INVALID after an out-of-range query id. */
 int cbfs_labels_status(cbfs_labels_t L, void* stream);
 
+/*
+ * Page-locked host memory for outputs and inputs (cudaHostAlloc, portable
+ * across devices).  No paper counterpart: host outputs of cbfs_run_batched
+ * overlap the traversal only from page-locked memory, and buffers pinned
+ * by some other allocators were measured to slow those overlapped copies
+ * down after earlier large jobs on the machine.  *host_out is NULL on
+ * failure (CBFS_E_NOMEM).  cbfs_host_free(NULL) is a no-op.
+ */
+int cbfs_host_alloc(size_t bytes, void** host_out);
+int cbfs_host_free(void* host_ptr);
+
 /* Human-readable name of a status code (static string). */
 const char* cbfs_status_string(int status);
 

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 from typing import Sequence
 
 import numpy as np
@@ -78,6 +79,8 @@ SIGNATURES = {
     "cbfs_query_local": (_I, [_P, _P, _P, _I64, _I, _P, _P]),
     "cbfs_labels_status": (_I, [_P, _P]),
     "cbfs_status_string": (ctypes.c_char_p, [_I]),
+    "cbfs_host_alloc": (_I, [_SZ, _P]),
+    "cbfs_host_free": (_I, [_P]),
 }
 
 
@@ -119,6 +122,21 @@ def _host_i32(a) -> np.ndarray:
     if isinstance(a, torch.Tensor):
         a = a.detach().cpu().numpy()
     return np.ascontiguousarray(np.asarray(a), dtype=np.int32)
+
+
+def pinned_empty(shape, dtype: torch.dtype) -> torch.Tensor:
+    """Uninitialised page-locked host tensor from ``cbfs_host_alloc``; the
+    memory is returned with ``cbfs_host_free`` once no tensor uses it."""
+    count = 1
+    for x in (shape if isinstance(shape, (tuple, list)) else (shape,)):
+        count *= int(x)
+    nbytes = max(count * torch.empty((), dtype=dtype).element_size(), 1)
+    p = ctypes.c_void_p()
+    _check(lib().cbfs_host_alloc(nbytes, ctypes.byref(p)), "cbfs_host_alloc")
+    buf = (ctypes.c_uint8 * nbytes).from_address(p.value)
+    weakref.finalize(buf, lib().cbfs_host_free, ctypes.c_void_p(p.value))
+    return torch.frombuffer(buf, dtype=torch.uint8)[:count * torch.empty((), dtype=dtype).element_size()].view(
+        dtype).view(*(shape if isinstance(shape, (tuple, list)) else (shape,)))
 
 
 def as_numpy_u64(t: torch.Tensor) -> np.ndarray:

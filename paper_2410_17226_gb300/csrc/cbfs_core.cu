@@ -1435,11 +1435,19 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     const bool staged = host_out || (L && !dist);
     const int64_t wave_dist = (int64_t)P * n;       // bytes
     const int64_t wave_masks = (int64_t)P * d * n;  // words
-    int G = 2;
-    if (staged && L) {
-        G = std::max(2, kLabelGroup / P);
+    // Host copies go out per group of CG waves (about 16 clusters: each D2H
+    // call has a fixed cost that grows with the state of the host's pinned
+    // memory), double-buffered in the ring so the next group traverses
+    // while the previous one is copied.
+    int G = 2, CG = 1;
+    if (staged) {
+        const int want_cg = host_out ? std::max(1, 16 / P) : 1;
+        if (L) G = std::max(2, kLabelGroup / P);
+        G = std::max(G, 2 * want_cg);
         const int64_t fit = kStageBudget / std::max<int64_t>(1, wave_dist + 8 * wave_masks);
         G = (int)std::max<int64_t>(2, std::min<int64_t>(G, fit));
+        CG = std::max(1, std::min(want_cg, G / 2));
+        while (G % CG) CG--;
     }
     const int LG = L ? (staged ? G : std::max(1, kLabelGroup / P)) : 0;  // waves per label write
     const int64_t stage_dist_bytes = (G * wave_dist + 255) / 256 * 256;
@@ -1674,17 +1682,20 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         ev = prof_begin(g, 0, st);
         CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
         prof_end(g, ev, st);
-        if (host_out) {
+        if (host_out && (rerun || (wv + 1) % CG == 0 || wv == nwaves - 1)) {
+            // the group's waves sit in consecutive ring slots (G is a multiple of CG)
+            const int g0 = rerun ? wv : wv / CG * CG;
+            const int64_t nc = (int64_t)std::min(C, (wv + 1) * P) - (int64_t)g0 * P;
             CK(cudaEventRecord(g->ev_emit[b], st));
             CK(cudaStreamWaitEvent(g->copy_stream, g->ev_emit[b], 0));
             if (dist)
-                CK(cudaMemcpyAsync(dist + (size_t)c0 * (size_t)n, wave_dist_at(wv), (size_t)w.nslots * (size_t)n,
+                CK(cudaMemcpyAsync(dist + (size_t)g0 * P * (size_t)n, wave_dist_at(g0), (size_t)nc * (size_t)n,
                                    cudaMemcpyDefault, g->copy_stream));
             if (masks && d)
-                CK(cudaMemcpyAsync(masks + (size_t)c0 * (size_t)d * (size_t)n, wave_masks_at(wv),
-                                   sizeof(uint64_t) * (size_t)w.nslots * (size_t)d * (size_t)n, cudaMemcpyDefault,
+                CK(cudaMemcpyAsync(masks + (size_t)g0 * P * (size_t)d * (size_t)n, wave_masks_at(g0),
+                                   sizeof(uint64_t) * (size_t)nc * (size_t)d * (size_t)n, cudaMemcpyDefault,
                                    g->copy_stream));
-            CK(cudaEventRecord(g->ev_copy[b], g->copy_stream));
+            for (int x = g0; x <= wv; ++x) CK(cudaEventRecord(g->ev_copy[x % G], g->copy_stream));
         }
         if (L) {
             if (rerun) {
@@ -1978,6 +1989,22 @@ int cbfs_run_batched_labels(cbfs_graph_t g, const int32_t* host_sources_concat, 
     if (!host_sources_concat || (!dist && masks) || (dist && d > 0 && !masks)) return CBFS_E_INVALID;
     return run_clusters(g, host_sources_concat, host_cluster_off, C, d, dist, masks, labels, tune,
                         (cudaStream_t)stream);
+}
+
+int cbfs_host_alloc(size_t bytes, void** host_out) {
+    if (!host_out) return CBFS_E_INVALID;
+    *host_out = nullptr;
+    if (cudaHostAlloc(host_out, std::max<size_t>(bytes, 1), cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        *host_out = nullptr;
+        return CBFS_E_NOMEM;
+    }
+    return CBFS_OK;
+}
+
+int cbfs_host_free(void* host_ptr) {
+    if (!host_ptr) return CBFS_OK;
+    return cudaFreeHost(host_ptr) == cudaSuccess ? CBFS_OK : CBFS_E_CUDA;
 }
 
 int cbfs_profile(cbfs_graph_t g, int enable, cbfs_kernel_times_t* host_out) {

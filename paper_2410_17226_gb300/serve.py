@@ -53,8 +53,8 @@ class _Slot:
 
     def __init__(self, max_batch: int, device):
         self.stream = torch.cuda.Stream(device=device)
-        self.h_pairs = torch.empty((max_batch, 2), dtype=torch.int32).pin_memory()
-        self.h_out = torch.empty(max_batch, dtype=torch.int16).pin_memory()
+        self.h_pairs = cbfs.pinned_empty((max_batch, 2), torch.int32)
+        self.h_out = cbfs.pinned_empty(max_batch, torch.int16)
         self.d_pairs = torch.empty((max_batch, 2), dtype=torch.int32, device=device)
         self.d_out = torch.empty(max_batch, dtype=torch.int16, device=device)
         self.event = torch.cuda.Event()

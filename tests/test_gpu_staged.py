@@ -59,6 +59,12 @@ def test_host_outputs_equal_device_outputs(cb, slots, host_loop):
         pin_m.fill_(7)
         g.run_batched(clusters, d, pin_d, pin_m, tune=tune)
         assert torch.equal(pin_d, ref_d) and torch.equal(pin_m, ref_m)
+    # page-locked buffers from the library's own allocator
+    lib_d = cb.pinned_empty((C, n), torch.uint8)
+    lib_m = cb.pinned_empty((C, d, n), torch.int64)
+    g.run_batched(clusters, d, lib_d, lib_m, tune=tune)
+    assert torch.equal(lib_d, ref_d) and torch.equal(lib_m, ref_m)
+    del lib_d, lib_m
     page_d = torch.full((C, n), 7, dtype=torch.uint8)
     page_m = torch.full((C, d, n), 7, dtype=torch.int64)
     g.run_batched(clusters, d, page_d, page_m, tune=tune)
