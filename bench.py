@@ -432,6 +432,43 @@ def ll_quality(cbfs, g, off, adj, seed: int, budget: int = 1024, n_src: int = 32
             "pairs_from": "the component of the highest-degree vertex", "by_index": out}
 
 
+def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per_launch: int = 16):
+    """The high-diameter road-like workload (4096 x 4096 grid, 10 % of edges
+    deleted, 1 % shortcuts; 64 BFS-ball clusters of 64 sources, d = their
+    largest exact diameter), timed in launches of `per_launch` clusters:
+    source-edge GTEPS and the algorithmic-byte rate beside the HBM peak."""
+    import torch
+
+    off, adj = I.road_grid(side, seed=I.MASTER_SEED + 2)
+    clusters, ds = I.ball_clusters(off, adj, count, 64, seed=seed)
+    d = max(ds)
+    deg = np.diff(off)
+    with cbfs.Graph(off, adj) as g:
+        n = g.n
+        dist = torch.empty((per_launch, n), dtype=torch.uint8, device="cuda")
+        masks = torch.empty((per_launch, d, n), dtype=torch.int64, device="cuda")
+        total_ms, A, V, src_edges, rounds = 0.0, 0, 0, 0, 0
+        for b in range(0, count, per_launch):
+            part = clusters[b:b + per_launch]
+            k = len(part)
+            run = lambda: g.run_batched(part, d, dist[:k], masks[:k])  # noqa: E731
+            total_ms += timed_ms(run, reps=2)
+            st = g.output_stats(dist[:k], masks[:k], [len(S) for S in part], d)
+            A += int(st[:, 1].sum())
+            V += int(st[:, 0].sum())
+            rounds = max(rounds, int(st[:, 3].max()))
+            reached = dist[:k].cpu().numpy() != 255
+            for c, S in enumerate(part):
+                src_edges += len(S) * int(deg[reached[c]].sum()) // 2
+        alg = ARC_BYTES * A + VERTEX_BYTES * V + count * n * (1 + 8 * d)
+        del dist, masks
+        torch.cuda.empty_cache()
+    return {"graph": f"road grid {side}x{side}, 10% deleted, 1% shortcuts", "n": int(n), "nnz": int(adj.size),
+            "clusters": count, "d": d, "per_launch": per_launch, "ms_all_clusters": round(total_ms, 2),
+            "gteps": round(src_edges / (total_ms / 1e3) / 1e9, 2), "max_rounds": rounds,
+            "alg_gbs": round(alg / (total_ms / 1e3) / 1e9, 1)}
+
+
 # ---------------------------------------------------------------- arms
 
 
@@ -631,6 +668,7 @@ def run_cbfs(args, ws, rank, local):
             sweep["road_grid_1024"] = d_sweep(cbfs, gg, goff, gadj, seed=rank_seed(rank) + 23)
         nxt["d_sweep"] = sweep
         nxt["ll_quality"] = ll_quality(cbfs, g, off, adj, seed=rank_seed(rank) + 24)
+        nxt["road_grid"] = road_grid_throughput(cbfs, seed=I.MASTER_SEED + 3)
 
     # serving (continuous batching) over labels of 60 degree-ordered clusters of the same graph
     serving = None
