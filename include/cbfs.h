@@ -28,7 +28,10 @@
  *     output is partially valid;
  *   - the graph is undirected: off/adj hold both arc directions.
  * The library is not thread-safe per handle: calls on one handle must not
- * overlap in time on the host.
+ * overlap in time on the host, and since a handle's scratch, class lists and
+ * staging buffers are reused by every call, calls on one handle should use
+ * one stream (or be ordered between streams by the caller).  Outputs of the
+ * traversal calls may also be host memory (see cbfs_run_batched).
  */
 #ifndef CBFS_H
 #define CBFS_H
