@@ -617,7 +617,10 @@ def run_cbfs(args, ws, rank, local):
         off_pin.copy_(torch.from_numpy(off))
         adj_pin = cbfs.pinned_empty(adj.shape, torch.int32)
         adj_pin.copy_(torch.from_numpy(adj))
-        e2e_host = (off_pin, adj_pin, cbfs.pinned_empty((C, n), torch.uint8), cbfs.pinned_empty((C, d, n), torch.int64))
+        # the 18 GB host-output variant only at N = 1 (N ranks on one node would pin N times that)
+        outs = (cbfs.pinned_empty((C, n), torch.uint8), cbfs.pinned_empty((C, d, n), torch.int64)) if ws == 1 \
+            else (None, None)
+        e2e_host = (off_pin, adj_pin) + outs
     g = cbfs.Graph(off, adj, validate=True)
     if args.fixed_tune:
         parts = args.fixed_tune.split(",")
@@ -835,19 +838,20 @@ def run_cbfs(args, ws, rank, local):
                                [round(1e3 * statistics.median(p[i] for p in parts), 2) for i in range(3)]))
 
         e_t, e_parts = e2e_run(False)
-        h_t, h_parts = e2e_run(True)
         e2e = {"value": round(src_edges / e_t / 1e9 * ws, 4), "unit": "GTEPS", "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(args.query_batch * 2), "ms_per_step": round(e_t * 1e3, 3),
                "includes": "graph create + validate from the page-locked host CSR; batched C-BFS of all clusters "
                            "writing the label store on the device (cbfs_run_batched_labels); query with pairs H2D "
                            "and answers D2H",
-               "ms_parts": e_parts,
-               "with_host_outputs": {
-                   "value": round(src_edges / h_t / 1e9 * ws, 4), "unit": "GTEPS", "ms_per_step": round(h_t * 1e3, 3),
-                   "d2h_bytes_per_step": int(dist_h.numel() + masks_h.numel() * 8 + args.query_batch * 2),
-                   "ms_parts": h_parts,
-                   "includes": "the same plus every cluster's dist/masks streamed into page-locked host memory "
-                               "(copies overlap later waves)"}}
+               "ms_parts": e_parts}
+        if dist_h is not None:
+            h_t, h_parts = e2e_run(True)
+            e2e["with_host_outputs"] = {
+                "value": round(src_edges / h_t / 1e9 * ws, 4), "unit": "GTEPS", "ms_per_step": round(h_t * 1e3, 3),
+                "d2h_bytes_per_step": int(dist_h.numel() + masks_h.numel() * 8 + args.query_batch * 2),
+                "ms_parts": h_parts,
+                "includes": "the same plus every cluster's dist/masks streamed into page-locked host memory "
+                            "(copies overlap later waves)"}
 
     # the other two workloads, last: one small cluster, and label construction
     # at scale 24 (its 0.5 GB-CSR generation churns host memory, which slows
