@@ -89,7 +89,11 @@ typedef struct cbfs_tune_s {
        (32, 16384); the autotuner picks them per graph. */
     int small_deg;
     int mid_deg;
-    int reserved[2];
+    /* warp-per-vertex limit for pull rounds whose frontier holds fewer than
+       n/32 vertices (lists rarely end early there).  0 or < 0 = use mid_deg
+       in every round (the default: other limits were measured no faster). */
+    int sparse_mid_deg;
+    int reserved[1];
 } cbfs_tune_t;
 
 /* Work counters of one cluster's traversal (Theorem 1). */

@@ -611,7 +611,15 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         return;
     }
 
-    // ---- pull: dense pass over every vertex that can still gain sources
+    // ---- pull: dense pass over every vertex that can still gain sources.
+    // Degree classes are consecutive rank ranges: big [0, nb), mid [nb, nb + nm),
+    // small [nb + nm, nb + nm + ns).
+    const bool sparse_round = w.n_big_s >= 0 && qlen * 32 < (unsigned long long)w.n;
+    const int64_t nb = sparse_round ? w.n_big_s : w.n_big;
+    const int64_t nm = sparse_round ? w.n_mid_s : w.n_mid;
+    const int64_t ns = sparse_round ? w.n_small_s : w.n_small;
+    const uint64_t* pieces = sparse_round ? w.pull_pieces_s : w.pull_pieces;
+    const int64_t npieces = sparse_round ? w.n_pull_pieces_s : w.n_pull_pieces;
     const unsigned int active = c->slot_active;
     unsigned long long my_cnt = 0, my_sdeg = 0;
     const uint64_t* all = sall;  // ALL of each slot, read from shared memory where needed
@@ -622,8 +630,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         __syncthreads();
         const unsigned int p = s_work;
         __syncthreads();
-        if (p >= w.n_pull_pieces) break;
-        const uint64_t pc = w.pull_pieces[p];
+        if (p >= npieces) break;
+        const uint64_t pc = pieces[p];
         const int32_t v = (int32_t)(pc >> 32);
         const int64_t o0 = w.off[v], o1 = w.off[v + 1];
         const int64_t a0 = o0 + (int64_t)(uint32_t)pc * kBigDeg;
@@ -690,8 +698,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nw_total = ((int64_t)gridDim.x * kThreads) >> 5;
     // warp per mid-degree vertex
-    for (int64_t i = gw; i < w.n_mid; i += nw_total) {
-        const int32_t v = w.pl_mid[i];
+    for (int64_t i = gw; i < nm; i += nw_total) {
+        const int32_t v = (int32_t)(nb + i);
         uint64_t vs[P];
         load_words<P>(w.vis + (size_t)v * P, vs);
         const unsigned int um = unfinished<P>(vs, all, active);
@@ -713,12 +721,13 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     // consecutive in the internal order, stages them in shared memory with
     // coalesced loads, then each lane scans its own list
     int32_t* wadj = sadj[wib];
-    for (int64_t g0 = gw * 32; g0 < w.n_small; g0 += nw_total * 32) {
+    const int64_t small0 = nb + nm;
+    for (int64_t g0 = gw * 32; g0 < ns; g0 += nw_total * 32) {
         const int64_t i = g0 + lane;
-        const bool has = i < w.n_small;
-        const int32_t v = has ? w.pl_small[i] : 0;
+        const bool has = i < ns;
+        const int32_t v = has ? (int32_t)(small0 + i) : 0;
         const int64_t o0 = has ? w.off[v] : 0, o1 = has ? w.off[v + 1] : 0;
-        const int last = (int)((w.n_small - 1 - g0) < 31 ? (w.n_small - 1 - g0) : 31);
+        const int last = (int)((ns - 1 - g0) < 31 ? (ns - 1 - g0) : 31);
         const int64_t lo = __shfl_sync(0xffffffffu, o0, 0);
         const int64_t hi = __shfl_sync(0xffffffffu, o1, last);
         for (int64_t x = lo + lane; x < hi; x += 32) wadj[x - lo] = w.adj[x];
@@ -742,7 +751,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         // the 32 vertices are consecutive: their bits span at most two bitmap words
         const unsigned int jm = __ballot_sync(0xffffffffu, joined);
         if (lane == 0 && jm) {
-            const int32_t v0 = w.pl_small[g0];
+            const int32_t v0 = (int32_t)(small0 + g0);
             const int sh = v0 & 31;
             atomicOr(fbn + (v0 >> 5), jm << sh);
             if (sh && (jm >> (32 - sh))) atomicOr(fbn + (v0 >> 5) + 1, jm >> (32 - sh));
@@ -933,15 +942,12 @@ struct cbfs_graph_s {
     uint8_t* dist_r = nullptr;   // internal output rows of a wave
     uint64_t* masks_r = nullptr;
     int64_t masks_r_cap = 0;
-    int32_t* pl = nullptr;  // pull lists: small | mid | big
     uint64_t* pull_pieces = nullptr;  // (rank << 32 | piece) of every vertex of degree > kPullMid
     int64_t n_small = 0, n_mid = 0, n_big = 0;  // degree classes of the default thresholds
     int64_t big_vertices = 0, big_pieces = 0;
-    // pull classes for the thresholds of the current call (cbfs_tune_t small_deg, mid_deg):
-    // pl holds them; hub piece lists are kept per mid threshold
+    // pull classes for a call's thresholds (cbfs_tune_t small_deg, mid_deg, sparse_mid_deg)
+    // are rank ranges sized from this histogram; hub piece lists are kept per mid threshold
     std::vector<unsigned long long> deg_count;  // vertices of degree 0..kMaxMidDeg, then above
-    int cls_small = 0, cls_mid = 0;
-    int64_t c_small = 0, c_mid = 0, c_big = 0;
     struct HubPieces {
         int mid;
         uint64_t* d;  // owned, except the create-time list (== pull_pieces)
@@ -1300,11 +1306,16 @@ void drop_graphs(cbfs_graph_s* g) {
 }
 
 // Pull classes for thresholds (small, mid): class sizes from the degree
-// histogram (ranks are sorted by degree, so each class is a rank range), the
-// rank lists rebuilt on the stream, the hub pieces (kBigDeg arcs each, in
-// piece-major order) built once per mid threshold.
-int ensure_classes(cbfs_graph_s* g, int small, int mid, cudaStream_t st) {
-    if (small == g->cls_small && mid == g->cls_mid) return CBFS_OK;
+// histogram (ranks are sorted by degree, so each class is a rank range) and
+// the hub pieces (kBigDeg arcs each, in piece-major order), built once per
+// mid threshold and cached.
+struct ClassSet {
+    int64_t c_small, c_mid, c_big;
+    const uint64_t* pieces;
+    int64_t npieces;
+};
+
+int class_set(cbfs_graph_s* g, int small, int mid, cudaStream_t st, ClassSet* out) {
     const auto& h = g->deg_count;
     unsigned long long total = 0, le_small = 0, le_mid = 0;
     for (int dg = 1; dg < (int)h.size(); ++dg) {
@@ -1312,51 +1323,50 @@ int ensure_classes(cbfs_graph_s* g, int small, int mid, cudaStream_t st) {
         if (dg <= small) le_small += h[dg];
         if (dg <= mid) le_mid += h[dg];
     }
-    const int64_t c_small = (int64_t)le_small, c_mid = (int64_t)(le_mid - le_small), c_big = (int64_t)(total - le_mid);
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    CK(class_lists(g->pl, c_small, c_mid, c_big, std::max(sms, 1), st));
-    bool have = false;
-    for (const auto& hp : g->pieces) have |= (hp.mid == mid);
-    if (!have) {
-        std::vector<int64_t> hub_off((size_t)c_big + 1, 0);
-        if (c_big > 0) {
-            CK(cudaMemcpyAsync(hub_off.data(), g->off_r, sizeof(int64_t) * hub_off.size(), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-        }
-        std::vector<uint64_t> pcs;
-        for (int64_t k = 0;; ++k) {
-            bool any = false;
-            for (int64_t r = 0; r < c_big; ++r) {
-                if (k * kBigDeg >= hub_off[(size_t)r + 1] - hub_off[(size_t)r]) break;  // degrees do not increase
-                pcs.push_back(((uint64_t)r << 32) | (uint64_t)k);
-                any = true;
-            }
-            if (!any) break;
-        }
-        cbfs_graph_s::HubPieces hp{mid, nullptr, (int64_t)pcs.size()};
-        int rc = dev_alloc(&hp.d, hp.count);
-        if (rc) return rc;
-        if (!pcs.empty()) {
-            CK(cudaMemcpyAsync(hp.d, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st));
-            CK(cudaStreamSynchronize(st));  // pcs dies with this scope
-        }
-        if (g->pieces.size() >= 8) {  // keep the create-time list, drop the oldest other one
-            for (size_t i = 0; i < g->pieces.size(); ++i) {
-                if (g->pieces[i].d == g->pull_pieces) continue;
-                drop_graphs(g);  // captured graphs may hold its address
-                dev_free(g->pieces[i].d);
-                g->pieces.erase(g->pieces.begin() + (long)i);
-                break;
-            }
-        }
-        g->pieces.push_back(hp);
+    out->c_small = (int64_t)le_small;
+    out->c_mid = (int64_t)(le_mid - le_small);
+    out->c_big = (int64_t)(total - le_mid);
+    for (const auto& hp : g->pieces) {
+        if (hp.mid != mid) continue;
+        out->pieces = hp.d;
+        out->npieces = hp.count;
+        return CBFS_OK;
     }
-    g->cls_small = small;
-    g->cls_mid = mid;
-    g->c_small = c_small;
-    g->c_mid = c_mid;
-    g->c_big = c_big;
+    const int64_t c_big = out->c_big;
+    std::vector<int64_t> hub_off((size_t)c_big + 1, 0);
+    if (c_big > 0) {
+        CK(cudaMemcpyAsync(hub_off.data(), g->off_r, sizeof(int64_t) * hub_off.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    std::vector<uint64_t> pcs;
+    for (int64_t k = 0;; ++k) {
+        bool any = false;
+        for (int64_t r = 0; r < c_big; ++r) {
+            if (k * kBigDeg >= hub_off[(size_t)r + 1] - hub_off[(size_t)r]) break;  // degrees do not increase
+            pcs.push_back(((uint64_t)r << 32) | (uint64_t)k);
+            any = true;
+        }
+        if (!any) break;
+    }
+    cbfs_graph_s::HubPieces hp{mid, nullptr, (int64_t)pcs.size()};
+    int rc = dev_alloc(&hp.d, hp.count);
+    if (rc) return rc;
+    if (!pcs.empty()) {
+        CK(cudaMemcpyAsync(hp.d, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // pcs dies with this scope
+    }
+    if (g->pieces.size() >= 8) {  // keep the create-time list, drop the oldest other one
+        for (size_t i = 0; i < g->pieces.size(); ++i) {
+            if (g->pieces[i].d == g->pull_pieces) continue;
+            drop_graphs(g);  // captured graphs may hold its address
+            dev_free(g->pieces[i].d);
+            g->pieces.erase(g->pieces.begin() + (long)i);
+            break;
+        }
+    }
+    g->pieces.push_back(hp);
+    out->pieces = hp.d;
+    out->npieces = hp.count;
     return CBFS_OK;
 }
 
@@ -1411,9 +1421,15 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     if (tune && tune->dense_div != 0) dense_div = tune->dense_div < 0 ? 0 : tune->dense_div;
     const int small_deg = (tune && tune->small_deg) ? tune->small_deg : (int)kPullSmall;
     const int mid_deg = (tune && tune->mid_deg) ? tune->mid_deg : kDefaultMidDeg;
+    // other classes for sparse pull rounds: off unless asked for (measured no faster warm)
+    const int sparse_mid = (tune && tune->sparse_mid_deg) ? tune->sparse_mid_deg : -1;
     if (small_deg < 1 || small_deg > (int)kPullSmall || mid_deg < small_deg || mid_deg > kMaxMidDeg)
         return CBFS_E_INVALID;
-    rc = ensure_classes(g, small_deg, mid_deg, st);
+    if (sparse_mid > 0 && (sparse_mid < small_deg || sparse_mid > kMaxMidDeg)) return CBFS_E_INVALID;
+    ClassSet cls, cls_s;
+    rc = class_set(g, small_deg, mid_deg, st, &cls);
+    if (!rc && sparse_mid > 0 && sparse_mid != mid_deg) rc = class_set(g, small_deg, sparse_mid, st, &cls_s);
+    else cls_s.c_big = -1;
     if (rc) return rc;
     rc = ensure_scratch(g, P);
     if (!rc) rc = ensure_dev(&g->masks_r, &g->masks_r_cap, std::max<int64_t>(1, g->n * d * P));
@@ -1535,16 +1551,17 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.big_fw = g->big_fw;
     w.piece_ent = g->piece_ent;
     w.piece_no = g->piece_no;
-    w.pl_small = g->pl;
-    w.pl_mid = g->pl + g->c_small;
-    w.pl_big = g->pl + g->c_small + g->c_mid;
-    w.n_small = g->c_small;
-    w.n_mid = g->c_mid;
-    w.n_big = g->c_big;
-    for (const auto& hp : g->pieces) {
-        if (hp.mid != g->cls_mid) continue;
-        w.pull_pieces = hp.d;
-        w.n_pull_pieces = hp.count;
+    w.n_small = cls.c_small;
+    w.n_mid = cls.c_mid;
+    w.n_big = cls.c_big;
+    w.pull_pieces = cls.pieces;
+    w.n_pull_pieces = cls.npieces;
+    w.n_big_s = cls_s.c_big;  // < 0: every pull round uses the classes above
+    if (cls_s.c_big >= 0) {
+        w.n_small_s = cls_s.c_small;
+        w.n_mid_s = cls_s.c_mid;
+        w.pull_pieces_s = cls_s.pieces;
+        w.n_pull_pieces_s = cls_s.npieces;
     }
     w.status = g->status;
     w.alpha = alpha;
@@ -1829,9 +1846,6 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     g->n_mid = (int64_t)hs.n_mid;
     g->n_big = (int64_t)hs.n_big;
     g->big_pieces = (int64_t)hs.big_pieces;
-    const int64_t nlist = g->n_small + g->n_mid + g->n_big;
-    rc = dev_alloc(&g->pl, nlist);
-    if (rc) return fail(rc);
     const void* kb[4] = {(const void*)k_phase_b<1>, (const void*)k_phase_b<2>, (const void*)k_phase_b<4>,
                          (const void*)k_phase_b<8>};
     for (int i = 0; i < 4; ++i) {
@@ -1868,7 +1882,6 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     if (e == cudaSuccess && nnz > 0)
         e = relabel_adjacency(n, g->n_big, g->n_mid, g->n_small, g->perm, g->iperm_d, g->off, g->adj, g->off_r, g->adj_r,
                               sms, st);
-    if (e == cudaSuccess) e = class_lists(g->pl, g->n_small, g->n_mid, g->n_big, sms, st);
     // degree histogram: class sizes of other thresholds without another pass
     g->deg_count.assign(kMaxMidDeg + 2, 0ull);
     if (e == cudaSuccess) e = degree_hist(n, g->off, reinterpret_cast<unsigned long long*>(scratch), sms, st);
@@ -1903,11 +1916,6 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
         e = cudaMemcpyAsync(g->pull_pieces, pcs.data(), sizeof(uint64_t) * pcs.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // pcs dies with this scope
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(CBFS_E_CUDA);
-    g->cls_small = (int)kPullSmall;
-    g->cls_mid = (int)kPullMid;
-    g->c_small = g->n_small;
-    g->c_mid = g->n_mid;
-    g->c_big = g->n_big;
     g->pieces.push_back({(int)kPullMid, g->pull_pieces, g->big_pieces});
     dev_free(scratch);
     dev_free(d_stats);
@@ -1931,7 +1939,6 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
         if (hp.d != g->pull_pieces) dev_free(hp.d);
     dev_free(g->pull_pieces);
     dev_free(g->masks_r);
-    dev_free(g->pl);
     dev_free(g->ctl);
     dev_free(g->status);
     dev_free(g->slots);

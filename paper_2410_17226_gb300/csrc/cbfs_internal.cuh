@@ -97,10 +97,12 @@ struct Wave {
     uint32_t* piece_ent;    // piece p covers arcs [piece_no*kBigDeg, ...) of big[piece_ent]
     uint32_t* piece_no;
     const uint64_t* pull_pieces;  // pull: (vertex << 32 | piece) for every kBigDeg-arc piece
-    int64_t n_pull_pieces;        //   of every vertex of degree > kPullMid
-    const int32_t* pl_small;  // pull lists: vertices by degree class, ascending ids
-    const int32_t* pl_mid;
-    const int32_t* pl_big;
+    int64_t n_pull_pieces;        //   of every vertex above the warp class
+    // pull rounds with a sparse frontier (qlen < n/32) use these classes instead when
+    // n_big_s >= 0 (a call's sparse_mid_deg; off by default)
+    int64_t n_small_s, n_mid_s, n_big_s;
+    const uint64_t* pull_pieces_s;
+    int64_t n_pull_pieces_s;
     int64_t n_small, n_mid, n_big;
     const int32_t* perm;    // internal vertex -> caller's id for the outputs (nullptr: identity)
     uint8_t* dist_r;        // [n][P] Delta rows of the wave in internal order, emitted to the
@@ -165,8 +167,6 @@ cudaError_t rank_order_device(int64_t n, const int64_t* off, uint64_t maxdeg, in
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t count, int64_t* out, int64_t* sums, cudaStream_t st);
 // Vertices of each degree 0..kMaxMidDeg, and above it in hist[kMaxMidDeg + 1].
 cudaError_t degree_hist(int64_t n, const int64_t* off, unsigned long long* hist, int sms, cudaStream_t st);
-// Pull lists in rank space: small | mid | big.
-cudaError_t class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big, int sms, cudaStream_t st);
 // Seeds hold callers' ids in their low 32 bits: rewrite them as ranks.
 cudaError_t map_seeds(uint64_t* seeds, int64_t count, const int32_t* iperm, cudaStream_t st);
 // Writes the relabelled adjacency (ranks, hubs first) of the ranks

@@ -108,6 +108,7 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
 
     Wave w;
     memset(&w, 0, sizeof(w));
+    w.n_big_s = -1;  // push only: no pull classes
     w.n = n;
     w.nnz = nnz;
     w.off = off;

@@ -365,19 +365,6 @@ __global__ void __launch_bounds__(kThreads) k_degree_hist(int64_t n, const int64
         if (bins[i]) atomicAdd(&hist[i], (unsigned long long)bins[i]);
 }
 
-// Pull lists in rank space, in the order small | mid | big: the degree
-// classes are consecutive rank ranges (big first).
-__global__ void k_class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big) {
-    const int64_t total = n_small + n_mid + n_big;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r;
-        if (i < n_small) r = n_big + n_mid + i;
-        else if (i < n_small + n_mid) r = n_big + (i - n_small);
-        else r = i - n_small - n_mid;
-        pl[i] = (int32_t)r;
-    }
-}
-
 __global__ void k_map_seeds(uint64_t* seeds, int64_t count, const int32_t* iperm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t e = seeds[i];
@@ -483,11 +470,6 @@ cudaError_t degree_hist(int64_t n, const int64_t* off, unsigned long long* hist,
         e = cudaGetLastError();
     }
     return e;
-}
-
-cudaError_t class_lists(int32_t* pl, int64_t n_small, int64_t n_mid, int64_t n_big, int sms, cudaStream_t st) {
-    if (n_small + n_mid + n_big > 0) k_class_lists<<<sms * 8, kThreads, 0, st>>>(pl, n_small, n_mid, n_big);
-    return cudaGetLastError();
 }
 
 cudaError_t map_seeds(uint64_t* seeds, int64_t count, const int32_t* iperm, cudaStream_t st) {

@@ -274,6 +274,10 @@ def test_pull_degree_classes_equal_oracle(cb, small, mid):
         for slots in (1, 4, 8):
             for tune in ({"slots": slots, "pull_alpha": 1e-9, "small_deg": small, "mid_deg": mid},
                          {"slots": slots, "small_deg": small, "mid_deg": mid, "host_loop": 1},
+                         {"slots": slots, "pull_alpha": 1e-9, "small_deg": small, "mid_deg": mid,
+                          "sparse_mid_deg": -1},  # the same classes in every pull round
+                         {"slots": slots, "pull_alpha": 1e-9, "small_deg": small, "mid_deg": mid,
+                          "sparse_mid_deg": max(small, 40)},  # other classes in sparse rounds
                          {"slots": slots, "pull_alpha": 1e-9}):  # back to the defaults
                 for _ in range(2):
                     dist, masks = g.run_batched(clusters, d, tune=tune)
