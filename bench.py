@@ -739,6 +739,24 @@ def run_cbfs(args, ws, rank, local):
     query = {"p50_ms": round(float(np.percentile(lat, 50)), 4), "p99_ms": round(float(np.percentile(lat, 99)), 4),
              "qps": round(qtot / q_wall, 1), "requests": len(lat), "clusters": C,
              "mode": "one request at a time, sizes U{1..65536}, pinned H2D + kernel + D2H"}
+    # the query kernel alone on a full batch: its algorithmic bytes are the
+    # pairs, the answers and both label rows, q * (8 + 2 + 2 * C * (1 + 8 d))
+    pairs_dev.copy_(pin_pairs)
+    reps = 20
+    L.query(pairs_dev, out=answers)
+    torch.cuda.synchronize()
+    qe0, qe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    qe0.record(stream)
+    for _ in range(reps):
+        L.query(pairs_dev, out=answers, stream=stream)
+    qe1.record(stream)
+    torch.cuda.synchronize()
+    q_ms = qe0.elapsed_time(qe1) / reps
+    q_alg = args.query_batch * (8 + 2 + 2 * C * (1 + 8 * d))
+    query["kernel"] = {"pairs": args.query_batch, "avg_launch_ms": round(q_ms, 4),
+                       "alg_bytes_per_launch": int(q_alg), "achieved_gbs": round(q_alg / (q_ms / 1e3) / 1e9, 1),
+                       "peak_gbs": peak, "frac": round(q_alg / (q_ms / 1e3) / 1e9 / peak, 4),
+                       "note": "random rows of 4.4 KB (256 clusters x 17 B): the label store (18 GB) exceeds L2"}
 
     # single-source BFS comparison and the d sweep (the same resident graph)
     nxt = None
@@ -894,6 +912,15 @@ def run_cbfs(args, ws, rank, local):
 
 
 def record_traffic(csv_path: str, clusters: int, note: str):
+    """Writes profiles/traffic.json from an ncu CSV (see traffic_from_csv)."""
+    out = traffic_from_csv(csv_path, clusters, note)
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+    return 0
+
+
+def traffic_from_csv(csv_path: str, clusters: int, note: str) -> dict:
     """DRAM bytes per cluster of the traversal kernels, from an ncu CSV of
     one host-driven `runcli` call, scaled to the bench's 256-cluster launch
     (traffic grows with the clusters at a fixed graph)."""
@@ -919,13 +946,9 @@ def record_traffic(csv_path: str, clusters: int, note: str):
         per_kernel[key] = per_kernel.get(key, 0.0) + v
         total += v
     per_cluster = total / clusters
-    out = {"traversal": {"dram_bytes_per_launch": int(per_cluster * 256), "per_cluster_bytes": int(per_cluster),
-                         "per_kernel_bytes": {k: int(v) for k, v in sorted(per_kernel.items())},
-                         "source_hash": kernel_source_hash(), "measured_on": note}}
-    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
-        json.dump(out, f, indent=1)
-    print(json.dumps(out))
-    return 0
+    return {"traversal": {"dram_bytes_per_launch": int(per_cluster * 256), "per_cluster_bytes": int(per_cluster),
+                          "per_kernel_bytes": {k: int(v) for k, v in sorted(per_kernel.items())},
+                          "source_hash": kernel_source_hash(), "measured_on": note}}
 
 
 def main():
