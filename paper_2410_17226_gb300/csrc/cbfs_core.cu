@@ -444,6 +444,9 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                         if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
                         else dr[s] = (uint8_t)round;
                         j = 0;
+                        // first visit of slot s: its subset words start empty here
+                        // (the rows are not cleared per wave; k_emit ignores unreached slots)
+                        for (int jj = 1; jj < w.d; ++jj) mr[(size_t)jj * P + s] = 0ull;
                     } else {
                         j = round - (int)dd;
                     }
@@ -781,13 +784,26 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
         const int64_t r = iperm ? iperm[v] : v;
         const uint8_t* dr = w.dist_r + (size_t)r * P;
         const uint64_t* mr = w.masks_r + (size_t)r * d * P;
-        for (int s = 0; s < w.nslots; ++s) ss[s].dist[v] = dr[s];
+        // a slot that never reached v has stale subset words in the row: write zeros
+        unsigned int reached = 0;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            if (s >= w.nslots) continue;
+            const uint8_t dv = dr[s];
+            ss[s].dist[v] = dv;
+            if (dv != 0xFF) reached |= 1u << s;
+        }
         for (int j = 0; j < d; ++j) {
             uint64_t m[P];
-            load_words<P>(mr + (size_t)j * P, m);
+            if (reached) {
+                load_words<P>(mr + (size_t)j * P, m);
+            } else {
+#pragma unroll
+                for (int s = 0; s < P; ++s) m[s] = 0ull;
+            }
 #pragma unroll
             for (int s = 0; s < P; ++s)
-                if (s < w.nslots) ss[s].masks[(size_t)j * (size_t)w.n + v] = m[s];
+                if (s < w.nslots) ss[s].masks[(size_t)j * (size_t)w.n + v] = ((reached >> s) & 1u) ? m[s] : 0ull;
         }
     }
 }
@@ -1211,7 +1227,6 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         if (e == cudaSuccess) e = cudaMemsetAsync(w.rq, 0, sizeof(uint32_t) * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.fb0, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.dist_r, 0xFF, (size_t)P * (size_t)n, cs);
-        if (e == cudaSuccess && d) e = cudaMemsetAsync(w.masks_r, 0, sizeof(uint64_t) * (size_t)P * d * n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, sizeof(RoundCtl) * kMaxRounds, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.round_dev, 0, sizeof(int), cs);
         if (e != cudaSuccess) break;
@@ -1653,7 +1668,6 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         CK(cudaMemsetAsync(g->rq, 0, sizeof(uint32_t) * (size_t)n, st));
         CK(cudaMemsetAsync(g->fb, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, st));
         CK(cudaMemsetAsync(g->dist_r, 0xFF, (size_t)P * (size_t)n, st));
-        if (d) CK(cudaMemsetAsync(g->masks_r, 0, sizeof(uint64_t) * (size_t)P * d * n, st));
         CK(cudaMemsetAsync(g->ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
         const int cnt = (int)(wave_seed_off[wv + 1] - wave_seed_off[wv]);
         int ev = prof_begin(g, 0, st);
