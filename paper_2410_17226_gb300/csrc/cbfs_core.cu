@@ -25,11 +25,14 @@
 //       entries are found by a binary search of the tile's arc prefix in
 //       shared memory.
 //     pull (EdgeMap-Dense): every vertex v with some unfinished slot ORs the
-//       vis blocks of all its neighbours (sources at distance <= i from a
-//       neighbour are at distance <= i+1 from v), stops early once every
+//       vis blocks of its frontier neighbours (a bitmap test, skipped when
+//       the frontier holds more than n/8 vertices: a non-frontier
+//       neighbour's sources are already in vis[v]), stops early once every
 //       unfinished slot is covered, and keeps the part not in vis[v] as
-//       acc[v].  Vertices are handled by a thread, a warp or a CTA according
-//       to their degree, each lane keeping four gathers in flight.
+//       acc[v].  Vertices are handled by a thread, a warp or 2048-arc CTA
+//       pieces according to their degree (thresholds per call, see
+//       cbfs_tune_t; ranks are sorted by degree, so each class is a rank
+//       range), each lane keeping four gathers in flight.
 //     The direction is chosen per round from |F| + sum deg(F) against
 //     pull_alpha * nnz (the rule of Algorithm "EdgeMap").
 //
