@@ -295,3 +295,45 @@ def test_pull_degree_classes_reject_bad_thresholds(cb):
         with pytest.raises(cb.CbfsError) as e:
             g.run_batched(clusters, d, tune={"small_deg": small, "mid_deg": mid})
         assert e.value.code == cb.E_INVALID
+
+
+def test_empty_graph_and_empty_calls(cb):
+    """n = 0: the graph builds, every source is out of range, zero clusters
+    and zero pairs are no-ops; on a small graph, zero clusters write nothing."""
+    off = np.zeros(1, np.int64)
+    adj = np.zeros(0, np.int32)
+    g = cb.Graph(off, adj)
+    assert g.n == 0 and g.nnz == 0
+    with pytest.raises(cb.CbfsError) as e:
+        g.run([0], 2)
+    assert e.value.code == cb.E_INVALID
+    dist, masks = g.run_batched([], 2)
+    assert dist.shape == (0, 0) and masks.shape == (0, 2, 0)
+    L = cb.Labels(0, 1, 2)
+    out = L.query(torch.zeros((0, 2), dtype=torch.int32, device="cuda"))
+    assert out.numel() == 0 and L.status() == cb.OK
+    off2, adj2 = I.path(20)
+    g2 = cb.Graph(off2, adj2)
+    d2 = torch.full((1, 20), 7, dtype=torch.uint8, device="cuda")
+    m2 = torch.full((1, 2, 20), 7, dtype=torch.int64, device="cuda")
+    g2.run_batched([], 2, d2, m2)
+    assert int(d2.min()) == 7 and int(m2.min()) == 7  # untouched
+
+
+@pytest.mark.parametrize("slots", [1, 4])
+def test_largest_diameter_bound(cb, slots):
+    """d = 15, the largest bound: sources 15 apart on a path and a grid
+    ball of diameter up to 15; every offset 0..15 occurs."""
+    off, adj = I.path(60)
+    g = cb.Graph(off, adj)
+    clusters = [np.array([10, 25], np.int32), np.array([0, 5, 15], np.int32), np.array([40, 55, 47], np.int32)]
+    dist, masks = g.run_batched(clusters, 15, tune={"slots": slots})
+    for c, S in enumerate(clusters):
+        od, om = O.cbfs_alg1(off, adj, S, 15)
+        assert (dist[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(masks[c]) == om).all()
+    goff, gadj = I.grid(20, 20)
+    gg = cb.Graph(goff, gadj)
+    S = np.array([0, 7, 8 * 20], np.int32)  # (0,0), (7,0), (0,8): 7, 8 and 15 apart
+    gd, gm = gg.run_batched([S], 15, tune={"slots": slots})
+    od, om = O.cbfs_alg1(goff, gadj, S, 15)
+    assert (gd[0].cpu().numpy() == od).all() and (cb.as_numpy_u64(gm[0]) == om).all()
