@@ -85,6 +85,23 @@ int scratch_for_device(int dev, unsigned char** out, int* grid) {
     return CBFS_OK;
 }
 
+// The caller's CSR is checked before any traversal kernel reads it through
+// its offsets: off[0] = 0, off[n] = nnz, offsets never decrease, every id in
+// [0, n).  Each read stays inside off[0..n] and adj[0..nnz), the sizes the
+// caller states.  The first failure writes CBFS_E_GRAPH to the status word.
+__global__ void k_noalloc_check(int64_t n, const int64_t* off, const int32_t* adj, int64_t nnz, int* status) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool ok = true;
+    if (tid == 0) ok = off[0] == 0 && off[n] == nnz;
+    for (int64_t v = tid; v < n; v += stride) ok &= off[v] <= off[v + 1];
+    for (int64_t e = tid; e < nnz; e += stride) {
+        const int32_t u = adj[e];
+        ok &= u >= 0 && (int64_t)u < n;
+    }
+    if (!ok) set_status(status, CBFS_E_GRAPH);
+}
+
 }  // namespace
 
 extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* adj, int64_t nnz,
@@ -166,16 +183,30 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     NA_CK(cudaMemsetAsync(w.fb0, 0, 8 * (size_t)kBitmapWords, st));
     NA_CK(cudaMemsetAsync(w.ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
     NA_CK(cudaMemsetAsync(w.status, 0, sizeof(int), st));
+    // the graph is checked before the traversal reads through its offsets and ids
+    k_noalloc_check<<<grid, kThreads, 0, st>>>(n, off, adj, nnz, w.status);
+    NA_CK(cudaGetLastError());
+    int status = 0;
+    // to pageable memory: returns once the copy (and the check before it) is done
+    NA_CK(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NA_CK(cudaStreamSynchronize(st));
+    if (status) return status;
     NA_CK(cudaMemsetAsync(dist, 0xFF, (size_t)n, st));
     if (d) NA_CK(cudaMemsetAsync(masks, 0, sizeof(uint64_t) * (size_t)d * (size_t)n, st));
     k_seed<<<1, kThreads, 0, st>>>(w, d_seeds, k);
     NA_CK(cudaGetLastError());
+    // Rounds are enqueued two at a time and the host looks at the frontier
+    // after each pair: a round whose frontier is empty returns at once, so the
+    // second round of the last pair costs two empty launches, and the host
+    // waits once per two levels instead of once per level.
     bool done = false;
-    for (int r = 0; r < kMaxRounds - 1; ++r) {
+    for (int r = 0; r + 1 < kMaxRounds - 1; r += 2) {
         NA_CK(launch_round(w, r, grid, st, 0));
         NA_CK(launch_round(w, r, grid, st, 1));
+        NA_CK(launch_round(w, r + 1, grid, st, 0));
+        NA_CK(launch_round(w, r + 1, grid, st, 1));
         unsigned long long qn = 0;
-        NA_CK(cudaMemcpyAsync(&qn, &w.ctl[r + 1].qlen, sizeof(qn), cudaMemcpyDeviceToHost, st));
+        NA_CK(cudaMemcpyAsync(&qn, &w.ctl[r + 2].qlen, sizeof(qn), cudaMemcpyDeviceToHost, st));
         NA_CK(cudaStreamSynchronize(st));
         if (qn == 0) {
             done = true;
@@ -185,7 +216,6 @@ extern "C" int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* ad
     if (!done) return CBFS_E_DEPTH;
     k_check_sources<<<1, kThreads, 0, st>>>(w, d_seeds, k, 0, nullptr);
     NA_CK(cudaGetLastError());
-    int status = 0;
     NA_CK(cudaMemcpyAsync(&status, w.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_CK(cudaStreamSynchronize(st));
 #undef NA_CK
