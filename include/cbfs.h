@@ -27,6 +27,17 @@
  *   - return value: CBFS_OK (0) or a negative CBFS_E_* status; on error no
  *     output is partially valid;
  *   - the graph is undirected: off/adj hold both arc directions.
+ * Stream ordering: the traversal calls with device outputs (cbfs_run,
+ * cbfs_run_batched), the label append and the queries only enqueue work on
+ * `stream` and return; their outputs are complete when the stream reaches
+ * that point.  Argument errors are returned at once.  Errors the kernels
+ * detect (CBFS_E_DIAMETER, CBFS_E_DEPTH, an out-of-range query id) are kept
+ * in a status word of the handle or label store -- the first one sticks --
+ * and returned by cbfs_sync_status(stream), or by the next call on the same
+ * handle that blocks; the outputs of a call that hit such an error are not
+ * valid.  Traversal calls with host outputs or a label store, host-driven
+ * rounds (cbfs_tune_t.host_loop) or kernel timing (cbfs_profile) block and
+ * return those errors themselves.
  * The library is not thread-safe per handle: calls on one handle must not
  * overlap in time on the host, and since a handle's scratch, class lists and
  * staging buffers are reused by every call, calls on one handle should use
@@ -84,9 +95,10 @@ typedef struct cbfs_tune_s {
        kernel timing enabled (cbfs_profile) always use the host loop. */
     int host_loop;
     /* degree classes of the dense edge phase: one thread per vertex of degree
-       <= small_deg (1..32), one warp per vertex of degree <= mid_deg
-       (small_deg..65536), one CTA per 2048-arc piece above.  0 = defaults
-       (32, 16384); the autotuner picks them per graph. */
+       <= small_deg (1..32, rounded down to a power of two), one warp per
+       vertex of degree <= mid_deg (small_deg..65536), one CTA per 2048-arc
+       piece above.  0 = defaults (32, 16384); the autotuner picks them per
+       graph. */
     int small_deg;
     int mid_deg;
     /* warp-per-vertex limit for pull rounds whose frontier holds fewer than
@@ -113,14 +125,21 @@ typedef struct cbfs_cluster_stats_s {
  * CBFS_E_GRAPH) on the device before returning.  Offsets that do not start
  * at 0, end at nnz and never decrease always give CBFS_E_GRAPH.  All work
  * after the copies (checks, degree order, relabelled copy) runs on the
- * device.  The call synchronises `stream`.  Limits: 0 <= n < 2^31,
- * 0 <= nnz < 2^40, every degree < 2^31.
+ * device.  The traversal runs on an internal copy whose vertices are ordered
+ * by degree, highest first, down to degree 32; vertices of degree 1..32
+ * follow in power-of-two buckets (32, 16, ..., 2, 1) that keep the caller's
+ * order within each bucket, then the isolated ones -- so graphs whose input
+ * order has locality (a grid in row-major order) keep most of it.  Outputs
+ * are always in the caller's ids.  The call synchronises `stream`.  Limits:
+ * 0 <= n < 2^31, 0 <= nnz < 2^40, every degree < 2^31.
  * Problem statement: Section 2 (unweighted graph G = (V, E)).
  */
 int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t* adj, int64_t nnz,
                       int inputs_on_device, int validate, void* stream, cbfs_graph_t* out);
 
-/* Frees the handle and everything it owns.  NULL is accepted. */
+/* Frees the handle and everything it owns, after the device has finished
+ * every call on it.  NULL is accepted.  No paper counterpart: it ends the
+ * residency of Section 2's graph G that cbfs_graph_create began. */
 int cbfs_graph_destroy(cbfs_graph_t g);
 
 /* n and nnz of the resident graph (host outputs). */
@@ -133,8 +152,13 @@ int cbfs_graph_info(cbfs_graph_t g, int64_t* host_n, int64_t* host_nnz);
  * Sources must be distinct and in [0, n); 1 <= k <= 64; 0 <= d <= 15.  d must
  * bound the pairwise source distances, otherwise CBFS_E_DIAMETER is returned
  * (the library detects the violation rather than producing wrong subsets).
- * The call returns when the outputs are complete (it synchronises `stream`).
- * Device scratch is owned by the handle and grown on demand.
+ * With device outputs the call is stream-ordered (see the top of this file):
+ * CBFS_E_DIAMETER and CBFS_E_DEPTH then come from cbfs_sync_status(stream).
+ * With host outputs it returns when they are complete.  Device scratch is
+ * owned by the handle and grown on demand (allocation synchronises the
+ * device; a call of the same size or smaller allocates nothing).  The first
+ * call of each call shape (clusters per wave, cluster sizes, d) records a
+ * CUDA graph of the traversal; later calls of that shape replay it.
  */
 int cbfs_run(cbfs_graph_t g, const int32_t* host_sources, int k, int d, uint8_t* dist, uint64_t* masks,
              void* stream);
@@ -149,11 +173,12 @@ int cbfs_run(cbfs_graph_t g, const int32_t* host_sources, int k, int d, uint8_t*
  * Same validation, errors and completion rule as cbfs_run.
  *
  * dist and masks may be device memory (written by the kernels) or host
- * memory.  With host memory every wave's outputs go to a device buffer and
- * are copied out on a second stream while the next wave traverses; pinned
+ * memory.  With device memory the call is stream-ordered, like cbfs_run.
+ * With host memory every wave's outputs go to a device buffer and are
+ * copied out on a second stream while the next wave traverses; pinned
  * memory (cudaHostAlloc / cudaHostRegister) lets the copies overlap,
- * pageable memory is correct but each copy blocks the calling thread.
- * Either way the outputs are complete when the call returns.
+ * pageable memory is correct but each copy blocks the calling thread; the
+ * outputs are complete when the call returns.
  */
 int cbfs_run_batched(cbfs_graph_t g, const int32_t* host_sources_concat, const int32_t* host_cluster_off,
                      int C, int d, uint8_t* dist, uint64_t* masks, const cbfs_tune_t* tune, void* stream);
@@ -182,7 +207,12 @@ int cbfs_run_batched_labels(cbfs_graph_t g, const int32_t* host_sources_concat, 
  *
  * The caller passes the graph directly (device off int64[n+1] and adj
  * int32[nnz], no handle), the sources on the host and the outputs (device
- * dist[n], masks[d][n]) exactly as for cbfs_run; the results are identical.
+ * dist[n], masks[d][n]) as for cbfs_run; the results are identical.  The
+ * graph is checked on the device before the traversal reads through it:
+ * off[0] = 0, off[n] = nnz, offsets that never decrease and ids in [0, n),
+ * else CBFS_E_GRAPH (the reads of the check stay inside off[0..n] and
+ * adj[0..nnz), so those two sizes must be right).  Symmetry is not checked:
+ * a directed CSR gives the C-BFS of its arcs.
  * The traversal's scratch is one fixed array compiled into the library
  * (about 7 MB; every GPU that loads the library keeps it until the process
  * exits), so the sizes are limited: n <= 131072 and nnz <= 4194304, larger
@@ -192,8 +222,8 @@ int cbfs_run_batched_labels(cbfs_graph_t g, const int32_t* host_sources_concat, 
  * call's contents (each call clears what must start at zero): calls that
  * overlap on the GPU -- on other streams or from other host threads -- race
  * and corrupt each other's results.  The edge phase runs in push mode only.
- * The call synchronises `stream`; it calls no cudaMalloc, cudaFree or other
- * allocating routine.
+ * The call synchronises `stream` (after the graph check, then once per two
+ * BFS levels); it calls no cudaMalloc, cudaFree or other allocating routine.
  */
 int cbfs_run_noalloc(int64_t n, const int64_t* off, const int32_t* adj, int64_t nnz, const int32_t* host_sources,
                      int k, int d, uint8_t* dist, uint64_t* masks, void* stream);
@@ -254,8 +284,10 @@ int cbfs_labels_destroy(cbfs_labels_t L);
 /*
  * Appends C clusters given in the cluster-major C-BFS output format (device
  * dist[C][n], masks[C][d][n]) with their sizes host_ks[C] (1..64) into the
- * vertex-major rows.  CBFS_E_INVALID when the store would exceed C_capacity.
- * Stream-ordered (asynchronous).
+ * vertex-major rows: the step of Section 4.2's Algorithm "Framework of
+ * Landmark Labeling" that stores each cluster's distance vectors in every
+ * vertex's label L[v].  CBFS_E_INVALID when the store would exceed
+ * C_capacity.  Stream-ordered (asynchronous).
  */
 int cbfs_labels_append(cbfs_labels_t L, const uint8_t* dist, const uint64_t* masks, const int32_t* host_ks,
                        int C, void* stream);
@@ -305,6 +337,64 @@ int cbfs_query_local(cbfs_labels_t L, cbfs_graph_t g, const int32_t* pairs, int6
  * status word: CBFS_OK or CBFS_E_INVALID after an out-of-range query id. */
 int cbfs_labels_status(cbfs_labels_t L, void* stream);
 
+/* Synchronises `stream` and returns (then clears) the graph handle's device
+ * status word: CBFS_OK or the first error its stream-ordered calls left
+ * (CBFS_E_DIAMETER, CBFS_E_DEPTH; CBFS_E_INVALID from a local-search query
+ * without labels).  Per handle, where cbfs_sync_status is per stream. */
+int cbfs_graph_status(cbfs_graph_t g, void* stream);
+
+/*
+ * Synchronises `stream`, then reads and clears the status words of every
+ * graph handle and label store that enqueued stream-ordered work on it since
+ * the last cbfs_sync_status of that stream, and returns CBFS_OK or the first
+ * error found (CBFS_E_DIAMETER, CBFS_E_DEPTH, CBFS_E_INVALID for a bad query
+ * id or seed), or CBFS_E_CUDA when the synchronisation itself fails.  The
+ * errors are those of Section 3.1's output definition: the distance vector
+ * of a vertex is only defined when d bounds the cluster's diameter
+ * (Corollary 1) and Delta_v fits the one byte Section 3.1 gives it.
+ */
+int cbfs_sync_status(void* stream);
+
+/*
+ * Distance-query server with continuous batching.  No paper counterpart: it
+ * serves the query of Section 4.2 ("Answering Queries with Clustered
+ * Landmarks", cbfs_query_distance) to requests that arrive at any time.
+ * A native dispatcher thread packs waiting requests, in arrival order, into
+ * batches of at most max_batch pairs and launches each on one of `slots`
+ * streams of its own (page-locked staging, H2D, the query kernel, D2H) as
+ * soon as a slot is free and the batch's device bytes fit the budget; one
+ * waiter thread per slot completes requests in the order their batches
+ * finish.  Memory: the server allocates its batch buffers at creation
+ * (10 bytes per pair: int32 pair + uint16 answer, slots x max_batch pairs)
+ * inside device_budget_bytes (0 = a quarter of the device memory free at
+ * creation; max_batch shrinks to fit), and admits a batch when the bytes in
+ * flight plus its own fit.  The label store must stay alive and unchanged
+ * while the server runs.
+ *
+ * cbfs_server_submit queues host_pairs[q][2] (int32, host memory) and gives
+ * a ticket; the answers go to host_out[q] (uint16, host memory).  Both
+ * buffers must stay valid until cbfs_server_wait has returned CBFS_OK for
+ * the ticket.  cbfs_server_wait blocks until the request is answered
+ * (timeout_s < 0: no limit) and releases the ticket, or returns
+ * CBFS_E_TIMEOUT and keeps it.  Out-of-range ids answer 0xFFFF and set the
+ * label store's status, as in cbfs_query_distance.  cbfs_server_stats
+ * fills host_counts[5] = (requests completed, batches, pairs answered,
+ * max_batch, budget bytes) and up to `cap` request latencies in
+ * milliseconds (arrival at cbfs_server_submit to answers in host_out), in
+ * completion order.  cbfs_server_destroy launches what is pending, waits for
+ * every batch in flight and frees the server; tickets not yet waited for
+ * become invalid.
+ */
+typedef struct cbfs_server_s* cbfs_server_t;
+int cbfs_server_create(cbfs_labels_t L, int64_t max_batch, int slots, size_t device_budget_bytes,
+                       cbfs_server_t* out);
+int cbfs_server_submit(cbfs_server_t S, const int32_t* host_pairs, int64_t q, uint16_t* host_out,
+                       uint64_t* ticket);
+int cbfs_server_wait(cbfs_server_t S, uint64_t ticket, double timeout_s);
+int cbfs_server_stats(cbfs_server_t S, uint64_t* host_counts, double* host_latency_ms, int64_t cap,
+                      int64_t* host_n_latency);
+int cbfs_server_destroy(cbfs_server_t S);
+
 /*
  * Page-locked host memory for outputs and inputs (cudaHostAlloc, portable
  * across devices).  No paper counterpart: host outputs of cbfs_run_batched
@@ -316,7 +406,8 @@ int cbfs_labels_status(cbfs_labels_t L, void* stream);
 int cbfs_host_alloc(size_t bytes, void** host_out);
 int cbfs_host_free(void* host_ptr);
 
-/* Human-readable name of a status code (static string). */
+/* Human-readable name of a status code (static string).  No paper
+ * counterpart: it names the codes of this interface. */
 const char* cbfs_status_string(int status);
 
 #ifdef __cplusplus

@@ -78,7 +78,14 @@ SIGNATURES = {
     "cbfs_query_distance": (_I, [_P, _P, _I64, _P, _P]),
     "cbfs_query_local": (_I, [_P, _P, _P, _I64, _I, _P, _P]),
     "cbfs_labels_status": (_I, [_P, _P]),
+    "cbfs_graph_status": (_I, [_P, _P]),
+    "cbfs_sync_status": (_I, [_P]),
     "cbfs_status_string": (ctypes.c_char_p, [_I]),
+    "cbfs_server_create": (_I, [_P, _I64, _I, _SZ, _P]),
+    "cbfs_server_submit": (_I, [_P, _P, _I64, _P, _P]),
+    "cbfs_server_wait": (_I, [_P, ctypes.c_uint64, ctypes.c_double]),
+    "cbfs_server_stats": (_I, [_P, _P, _P, _I64, _P]),
+    "cbfs_server_destroy": (_I, [_P]),
     "cbfs_host_alloc": (_I, [_SZ, _P]),
     "cbfs_host_free": (_I, [_P]),
 }
@@ -203,8 +210,22 @@ class Graph:
         self.close()
 
     # -- traversal -----------------------------------------------------------
+    # The traversal calls are stream-ordered in the C ABI.  With check=True
+    # (the default) the binding then waits for the stream and raises on an
+    # error the kernels detected (cbfs_graph_status); with check=False it
+    # returns at once and such errors come from status() or sync_status().
+    def _checked(self, rc: int, where: str, check: bool, stream):
+        _check(rc, where)
+        if check:
+            _check(lib().cbfs_graph_status(self._h, _stream_ptr(stream)), where)
+
+    def status(self, stream=None) -> int:
+        """``cbfs_graph_status``: waits for ``stream``, returns and clears the
+        handle's device status word."""
+        return int(lib().cbfs_graph_status(self._h, _stream_ptr(stream)))
+
     def run(self, sources, d: int, dist: torch.Tensor | None = None, masks: torch.Tensor | None = None,
-            stream=None):
+            stream=None, check: bool = True):
         """One C-BFS (``cbfs_run``).  Returns ``(dist uint8[n], masks int64[d, n])``."""
         S = _host_i32(sources)
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -214,7 +235,7 @@ class Graph:
             masks = torch.empty((max(d, 0), self.n), dtype=torch.int64, device=dev)
         rc = lib().cbfs_run(self._h, S.ctypes.data, int(S.size), int(d), _ptr(dist),
                             _ptr(masks) if d > 0 else None, _stream_ptr(stream))
-        _check(rc, "cbfs_run")
+        self._checked(rc, "cbfs_run", check, stream)
         return dist, masks
 
     @staticmethod
@@ -242,7 +263,7 @@ class Graph:
 
     def run_batched(self, clusters: Sequence | None, d: int, dist: torch.Tensor | None = None,
                     masks: torch.Tensor | None = None, tune: dict | None = None, stream=None,
-                    sources_concat=None, cluster_off=None):
+                    sources_concat=None, cluster_off=None, check: bool = True):
         """C clusters in one call (``cbfs_run_batched``).  ``clusters`` is a list
         of source arrays; alternatively pass ``sources_concat`` and
         ``cluster_off`` (the C ABI's layout) with ``clusters=None``.  ``dist``
@@ -260,7 +281,7 @@ class Graph:
         src_p = src.ctypes.data if src.size else np.zeros(1, np.int32).ctypes.data
         rc = lib().cbfs_run_batched(self._h, src_p, coff.ctypes.data, int(C), int(d), _ptr(dist),
                                     _ptr(masks) if d > 0 else None, ctypes.byref(t), _stream_ptr(stream))
-        _check(rc, "cbfs_run_batched")
+        self._checked(rc, "cbfs_run_batched", check, stream)
         return dist, masks
 
     def run_batched_labels(self, clusters: Sequence | None, d: int, labels: "Labels", dist: torch.Tensor | None = None,
@@ -317,6 +338,35 @@ class Graph:
                         dtype=np.int64).reshape(C, 4)
 
 
+def _check_noalloc_args(off, adj, d, dist, masks):
+    """Types, sizes and devices of run_noalloc's tensors (ValueError)."""
+    named = {"off": off, "adj": adj, "dist": dist}
+    if d > 0:
+        named["masks"] = masks
+    want = {"off": torch.int64, "adj": torch.int32, "dist": torch.uint8, "masks": torch.int64}
+    for name, t in named.items():
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"run_noalloc: {name} must be a torch.Tensor")
+        if t.dtype != want[name]:
+            raise ValueError(f"run_noalloc: {name} must be {want[name]}, got {t.dtype}")
+    if off.dim() != 1 or off.numel() < 2:
+        raise ValueError("run_noalloc: off must be 1-D with n + 1 >= 2 entries")
+    if adj.dim() != 1:
+        raise ValueError("run_noalloc: adj must be 1-D")
+    n = off.numel() - 1
+    if dist.numel() != n:
+        raise ValueError(f"run_noalloc: dist has {dist.numel()} entries, the graph {n} vertices")
+    if d > 0 and tuple(masks.shape) != (d, n):
+        raise ValueError(f"run_noalloc: masks has shape {tuple(masks.shape)}, expected {(d, n)}")
+    for name, t in named.items():
+        if not t.is_cuda:
+            raise ValueError(f"run_noalloc: {name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"run_noalloc: {name} must be contiguous")
+        if t.device != off.device:
+            raise ValueError(f"run_noalloc: {name} is on {t.device}, off on {off.device}")
+
+
 def run_noalloc(off: torch.Tensor, adj: torch.Tensor, sources, d: int, dist: torch.Tensor, masks: torch.Tensor,
                 stream=None):
     """``cbfs_run_noalloc``: one C-BFS for callers that cannot allocate device
@@ -324,7 +374,10 @@ def run_noalloc(off: torch.Tensor, adj: torch.Tensor, sources, d: int, dist: tor
     caller owns; ``dist`` (uint8, n) and ``masks`` (int64, d x n) are
     preallocated CUDA tensors that receive the outputs.  The library uses a
     fixed scratch array (n <= 131072, nnz <= 4194304) shared by all calls, so
-    calls must not overlap on the GPU."""
+    calls must not overlap on the GPU.  Tensors of another type, shape or
+    device raise ValueError before the library is called: the C entry point
+    takes raw pointers and would read or write past a wrong-sized buffer."""
+    _check_noalloc_args(off, adj, d, dist, masks)
     S = _host_i32(sources)
     n = off.numel() - 1
     rc = lib().cbfs_run_noalloc(int(n), _ptr(off), _ptr(adj) if adj.numel() else None, int(adj.numel()),
@@ -400,3 +453,10 @@ class Labels:
 
 def status_string(code: int) -> str:
     return lib().cbfs_status_string(int(code)).decode()
+
+
+def sync_status(stream=None) -> int:
+    """``cbfs_sync_status``: waits for ``stream`` and returns (then clears) the
+    first error left by stream-ordered calls of any handle or label store on
+    it (``OK`` when none)."""
+    return int(lib().cbfs_sync_status(_stream_ptr(stream)))

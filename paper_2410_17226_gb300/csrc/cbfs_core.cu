@@ -50,6 +50,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -999,12 +1000,22 @@ struct cbfs_graph_s {
     int64_t slots_cap = 0;
     uint64_t* seeds = nullptr;
     int64_t seeds_cap = 0;
-    // pinned host staging
+    // pinned host staging: the slot tables and seeds of a call are uploaded
+    // from ring entry (call number % kUploadRing); a call waits for the upload
+    // of the call kUploadRing calls earlier before it rewrites that entry, so
+    // stream-ordered calls can be queued without the host overwriting a copy
+    // still in flight
     unsigned long long* h_q = nullptr;  // [kMaxRounds + 2]
-    SlotDesc* h_slots = nullptr;
-    int64_t h_slots_cap = 0;
-    uint64_t* h_seeds = nullptr;
-    int64_t h_seeds_cap = 0;
+    static constexpr int kUploadRing = 4;
+    struct Upload {
+        SlotDesc* slots = nullptr;
+        int64_t slots_cap = 0;
+        uint64_t* seeds = nullptr;
+        int64_t seeds_cap = 0;
+        cudaEvent_t done = nullptr;
+    };
+    Upload up[kUploadRing];
+    uint64_t calls = 0;
     // kernel accounting (cbfs_profile)
     bool timing = false;
     std::vector<cudaEvent_t> events;  // pool, reused every call
@@ -1021,9 +1032,9 @@ struct cbfs_graph_s {
     struct GraphEntry {
         uint64_t key;
         cudaGraphExec_t exec;
+        cudaEvent_t done;  // recorded after the latest launch: an evicted graph is destroyed once it has run
     };
     std::vector<GraphEntry> graphs;  // most recently used last
-    std::vector<uint64_t> seen;      // call shapes run once (host-driven) and not yet captured
     int* wave_flags = nullptr;       // host-driven: waves that needed more rounds than enqueued
     int64_t wave_flags_cap = 0;
     // staged outputs (host destinations, or labels without outputs): a ring
@@ -1311,16 +1322,46 @@ int graph_view(const cbfs_graph_s* g, GraphView* out) {
 
 int* graph_status(cbfs_graph_s* g) { return g->status; }
 
+// (status words registered per stream by stream-ordered calls)
+struct PendingStatus {
+    cudaStream_t stream;
+    int* word;
+    const void* owner;
+};
+static std::mutex g_pending_mu;
+static std::vector<PendingStatus> g_pending;
+
+void status_register(cudaStream_t st, int* word, const void* owner) {
+    std::lock_guard<std::mutex> lock(g_pending_mu);
+    for (const auto& p : g_pending)
+        if (p.stream == st && p.word == word) return;
+    g_pending.push_back({st, word, owner});
+}
+
+void status_forget(const void* owner) {
+    std::lock_guard<std::mutex> lock(g_pending_mu);
+    g_pending.erase(std::remove_if(g_pending.begin(), g_pending.end(),
+                                   [owner](const PendingStatus& p) { return p.owner == owner; }),
+                    g_pending.end());
+}
+
 }  // namespace cbfs
 
 namespace {
 
-// Forgets every captured graph of the handle (and the call shapes seen once).
+// Destroys one cached graph once its latest launch has run.
+void destroy_graph(cbfs_graph_s::GraphEntry& ge) {
+    if (ge.done) {
+        cudaEventSynchronize(ge.done);
+        cudaEventDestroy(ge.done);
+    }
+    cudaGraphExecDestroy(ge.exec);
+}
+
+// Forgets every captured graph of the handle.
 void drop_graphs(cbfs_graph_s* g) {
-    if (!g->graphs.empty()) cudaDeviceSynchronize();  // a replay may still be in flight
-    for (auto& ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+    for (auto& ge : g->graphs) destroy_graph(ge);
     g->graphs.clear();
-    g->seen.clear();
 }
 
 // Pull classes for thresholds (small, mid): class sizes from the degree
@@ -1411,7 +1452,7 @@ int run_clusters(cbfs_graph_s* g, const int32_t* src, const int32_t* coff, int C
     CK(cudaSetDevice(g->device));
     int lbase = 0;
     if (L) {
-        rc = labels_reserve(L, g->n, d, coff, C, &lbase);
+        rc = labels_reserve(L, g->n, d, coff, C, &lbase, st);
         if (rc) return rc;
     }
     rc = run_clusters_inner(g, src, coff, C, d, dist, masks, L, lbase, tune, st);
@@ -1437,7 +1478,11 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     };
     int dense_div = 16;
     if (tune && tune->dense_div != 0) dense_div = tune->dense_div < 0 ? 0 : tune->dense_div;
-    const int small_deg = (tune && tune->small_deg) ? tune->small_deg : (int)kPullSmall;
+    int small_deg = (tune && tune->small_deg) ? tune->small_deg : (int)kPullSmall;
+    // degrees up to kPullSmall are ordered by power-of-two bucket (cbfs_relabel.cu):
+    // the thread class ends at a bucket boundary to stay a rank range
+    if (small_deg >= 1 && small_deg <= (int)kPullSmall)
+        while (small_deg & (small_deg - 1)) small_deg &= small_deg - 1;
     const int mid_deg = (tune && tune->mid_deg) ? tune->mid_deg : kDefaultMidDeg;
     // other classes for sparse pull rounds: off unless asked for (measured no faster warm)
     const int sparse_mid = (tune && tune->sparse_mid_deg) ? tune->sparse_mid_deg : -1;
@@ -1508,12 +1553,16 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     // Captured graphs hold these device pointers: when one of them moves, every
     // cached graph goes (a replay would read the freed buffer).
     const void* held[2] = {g->slots, g->seeds};
+    cbfs_graph_s::Upload& up = g->up[g->calls % cbfs_graph_s::kUploadRing];
+    if (up.done) CK(cudaEventSynchronize(up.done));  // this entry's previous upload has been read
     rc = ensure_dev(&g->slots, &g->slots_cap, (int64_t)nwaves * P);
-    if (!rc) rc = ensure_pinned(&g->h_slots, &g->h_slots_cap, (int64_t)nwaves * P);
+    if (!rc) rc = ensure_pinned(&up.slots, &up.slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_dev(&g->seeds, &g->seeds_cap, total_src);
-    if (!rc) rc = ensure_pinned(&g->h_seeds, &g->h_seeds_cap, total_src);
+    if (!rc) rc = ensure_pinned(&up.seeds, &up.seeds_cap, total_src);
     if (held[0] != (const void*)g->slots || held[1] != (const void*)g->seeds) drop_graphs(g);
     if (rc) return rc;
+    if (!up.done) CK(cudaEventCreateWithFlags(&up.done, cudaEventDisableTiming));
+    g->calls += 1;
     // slot tables and seeds of every wave, staged once
     std::vector<int64_t> wave_seed_off(nwaves + 1, 0);
     int64_t ns = 0;
@@ -1530,17 +1579,20 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                 sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
                 sd.cluster = c;
                 for (int j = 0; j < k; ++j)
-                    g->h_seeds[ns++] = ((uint64_t)s << 40) | ((uint64_t)j << 32) | (uint32_t)src[coff[c] + j];  // mapped to ranks on the device
+                    up.seeds[ns++] = ((uint64_t)s << 40) | ((uint64_t)j << 32) | (uint32_t)src[coff[c] + j];  // mapped to ranks on the device
             }
-            g->h_slots[(size_t)wv * P + s] = sd;
+            up.slots[(size_t)wv * P + s] = sd;
         }
     }
     wave_seed_off[nwaves] = ns;
-    CK(cudaMemcpyAsync(g->slots, g->h_slots, sizeof(SlotDesc) * (size_t)nwaves * P, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(g->seeds, g->h_seeds, sizeof(uint64_t) * (size_t)std::max<int64_t>(ns, 1),
+    CK(cudaMemcpyAsync(g->slots, up.slots, sizeof(SlotDesc) * (size_t)nwaves * P, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g->seeds, up.seeds, sizeof(uint64_t) * (size_t)std::max<int64_t>(ns, 1),
                        cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(up.done, st));
     CK(map_seeds(g->seeds, ns, g->iperm_d, st));
-    CK(cudaMemsetAsync(g->status, 0, sizeof(int), st));
+    // The status word is sticky: it is not cleared here, so an error of an
+    // earlier stream-ordered call stays until cbfs_sync_status or the next
+    // blocking call reads (and clears) it.
 
     Wave w;
     memset(&w, 0, sizeof(w));
@@ -1587,14 +1639,16 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.masks_r = g->masks_r;
     w.dense_div = dense_div;
 
-    // Graph mode: a call shape seen before runs as one cached CUDA graph whose
-    // rounds loop on the device; a first sighting runs host-driven below and
-    // is remembered, so one-off calls (a fresh handle) pay no capture.
+    // Graph mode (device outputs): the call runs as one cached CUDA graph per
+    // call shape whose rounds loop on the device, and is stream-ordered: the
+    // graph is launched on `st` and the call returns.  Device-detected errors
+    // stay in the status word for cbfs_sync_status(st) or the next blocking call.
     if (!g->timing && !(tune && tune->host_loop) && !staged && !L) {
         if (!g->round_dev) {
             rc = dev_alloc(&g->round_dev, 1);
             if (!rc) rc = dev_alloc(&g->iters, 1);
             if (rc) return rc;
+            CK(cudaMemsetAsync(g->iters, 0, sizeof(unsigned long long), st));  // rounds run, read by cbfs_profile
         }
         Wave wg = w;
         wg.round_dev = g->round_dev;
@@ -1610,47 +1664,41 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         key = fnv1a(key, wave_seed_off.data(), sizeof(int64_t) * wave_seed_off.size());
         key = fnv1a(key, &grid, sizeof(grid));
         key = fnv1a(key, &g->seeds, sizeof(g->seeds));  // baked into k_seed / k_check_sources
-        cudaGraphExec_t exec = nullptr;
+        cbfs_graph_s::GraphEntry* ge = nullptr;
         for (size_t i = 0; i < g->graphs.size(); ++i) {
             if (g->graphs[i].key == key) {
-                const auto ge = g->graphs[i];
+                const auto hit = g->graphs[i];
                 g->graphs.erase(g->graphs.begin() + (long)i);
-                g->graphs.push_back(ge);
-                exec = ge.exec;
+                g->graphs.push_back(hit);
+                ge = &g->graphs.back();
                 break;
             }
         }
-        if (!exec) {
-            bool repeat = false;
-            for (uint64_t k : g->seen) repeat |= (k == key);
-            if (repeat) {
-                rc = build_graph(g, waves, wave_seed_off, grid, bm_words, &exec);
-                if (rc) return rc;
-                if (g->graphs.size() >= 8) {
-                    cudaGraphExecDestroy(g->graphs.front().exec);
-                    g->graphs.erase(g->graphs.begin());
-                }
-                g->graphs.push_back({key, exec});
-            } else {
-                if (g->seen.size() >= 16) g->seen.erase(g->seen.begin());
-                g->seen.push_back(key);
+        if (!ge) {
+            cudaGraphExec_t exec = nullptr;
+            rc = build_graph(g, waves, wave_seed_off, grid, bm_words, &exec);
+            if (rc) return rc;
+            cudaEvent_t done = nullptr;
+            if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(exec);
+                return CBFS_E_CUDA;
             }
+            if (g->graphs.size() >= 8) {
+                destroy_graph(g->graphs.front());
+                g->graphs.erase(g->graphs.begin());
+            }
+            g->graphs.push_back({key, exec, done});
+            ge = &g->graphs.back();
         }
-        if (exec) {
-            CK(cudaMemsetAsync(g->iters, 0, sizeof(unsigned long long), st));
-            CK(cudaGraphLaunch(exec, st));
-            int status = 0;
-            unsigned long long iters = 0;
-            CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CK(cudaMemcpyAsync(&iters, g->iters, sizeof(iters), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            // per wave: seed, emit, check; per round: phase A, phase B, condition
-            g->launches[0] += 3ull * (uint64_t)nwaves;
-            g->launches[1] += iters;
-            g->launches[2] += iters;
-            g->total_launches += 3ull * (uint64_t)nwaves + 3ull * iters;
-            return status;
-        }
+        CK(cudaGraphLaunch(ge->exec, st));
+        CK(cudaEventRecord(ge->done, st));
+        status_register(st, g->status, g);
+        // per wave: seed, emit, check; the rounds' three launches are counted
+        // on the device and added by cbfs_profile
+        g->launches[0] += 3ull * (uint64_t)nwaves;
+        g->total_launches += 3ull * (uint64_t)nwaves;
+        return CBFS_OK;
     }
 
     // Host-driven rounds.  A "careful" wave synchronises every two rounds to
@@ -1770,8 +1818,11 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     }
     if (host_out)
         for (int b = 0; b < G; ++b) CK(cudaStreamWaitEvent(st, g->ev_copy[b], 0));
+    // a blocking call returns (and clears) the status word, including an error
+    // left by an earlier stream-ordered call that nobody has read yet
     int status = 0;
     CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemsetAsync(g->status, 0, sizeof(int), st));
     CK(cudaStreamSynchronize(st));
     prof_collect(g);
     return status;
@@ -1943,6 +1994,7 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
 
 int cbfs_graph_destroy(cbfs_graph_t g) {
     if (!g) return CBFS_OK;
+    status_forget(g);
     cudaSetDevice(g->device);
     cudaDeviceSynchronize();
     free_scratch(g);
@@ -1961,7 +2013,7 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->slots);
     dev_free(g->seeds);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
-    for (auto& ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+    drop_graphs(g);
     dev_free(g->stage);
     if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
     for (cudaEvent_t e : g->ev_emit) cudaEventDestroy(e);
@@ -1972,8 +2024,11 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->iters);
     dev_free(g->wave_flags);
     if (g->h_q) cudaFreeHost(g->h_q);
-    if (g->h_slots) cudaFreeHost(g->h_slots);
-    if (g->h_seeds) cudaFreeHost(g->h_seeds);
+    for (auto& u : g->up) {
+        if (u.slots) cudaFreeHost(u.slots);
+        if (u.seeds) cudaFreeHost(u.seeds);
+        if (u.done) cudaEventDestroy(u.done);
+    }
     delete g;
     return CBFS_OK;
 }
@@ -2015,6 +2070,42 @@ int cbfs_run_batched_labels(cbfs_graph_t g, const int32_t* host_sources_concat, 
                         (cudaStream_t)stream);
 }
 
+int cbfs_graph_status(cbfs_graph_t g, void* stream) {
+    if (!g) return CBFS_E_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemsetAsync(g->status, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    return h;
+}
+
+int cbfs_sync_status(void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st));
+    std::vector<PendingStatus> mine;
+    {
+        std::lock_guard<std::mutex> lock(g_pending_mu);
+        for (size_t i = 0; i < g_pending.size();) {
+            if (g_pending[i].stream == st) {
+                mine.push_back(g_pending[i]);
+                g_pending.erase(g_pending.begin() + (long)i);
+            } else {
+                ++i;
+            }
+        }
+    }
+    int first = CBFS_OK;
+    for (const auto& p : mine) {
+        int h = 0;
+        CK(cudaMemcpyAsync(&h, p.word, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemsetAsync(p.word, 0, sizeof(int), st));
+        CK(cudaStreamSynchronize(st));
+        if (h != CBFS_OK && first == CBFS_OK) first = h;
+    }
+    return first;
+}
+
 int cbfs_host_alloc(size_t bytes, void** host_out) {
     if (!host_out) return CBFS_E_INVALID;
     *host_out = nullptr;
@@ -2033,6 +2124,17 @@ int cbfs_host_free(void* host_ptr) {
 
 int cbfs_profile(cbfs_graph_t g, int enable, cbfs_kernel_times_t* host_out) {
     if (!g) return CBFS_E_INVALID;
+    if (g->iters) {
+        // rounds run by graph-mode calls since the last read (three launches each)
+        unsigned long long it = 0;
+        CK(cudaSetDevice(g->device));
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(&it, g->iters, sizeof(it), cudaMemcpyDeviceToHost));
+        CK(cudaMemset(g->iters, 0, sizeof(it)));
+        g->launches[1] += it;
+        g->launches[2] += it;
+        g->total_launches += 3ull * it;
+    }
     if (host_out) {
         for (int i = 0; i < 3; ++i) {
             host_out->launches[i] = g->launches[i];

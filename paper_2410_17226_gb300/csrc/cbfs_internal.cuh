@@ -190,7 +190,7 @@ int* graph_status(cbfs_graph_s* g);  // the handle's device status word
 // Label store (cbfs_labels.cu) fed by a batched run: reserve C rows' worth of
 // clusters at the store's count (uploads their ALL words), write nc clusters
 // of cluster-major outputs at position pos, or undo a reservation.
-int labels_reserve(cbfs_labels_s* L, int64_t n, int d, const int32_t* coff, int C, int* base);
+int labels_reserve(cbfs_labels_s* L, int64_t n, int d, const int32_t* coff, int C, int* base, cudaStream_t st);
 cudaError_t labels_write(cbfs_labels_s* L, const uint8_t* dist, const uint64_t* masks, int nc, int pos,
                          cudaStream_t st);
 void labels_rollback(cbfs_labels_s* L, int base);
@@ -198,6 +198,13 @@ void labels_rollback(cbfs_labels_s* L, int base);
 // Launches phase A (which = 0), phase B (1) of one round, or the emit
 // kernel (2) for w.P (1, 2, 4 or 8).
 cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which, const int32_t* iperm = nullptr);
+
+// Stream-ordered calls leave device-detected errors in their owner's status
+// word (a graph handle's or a label store's); cbfs_sync_status(stream) reads
+// and clears the words registered for that stream.  status_forget drops an
+// owner's entries when it is destroyed.  (cbfs_core.cu)
+void status_register(cudaStream_t st, int* word, const void* owner);
+void status_forget(const void* owner);
 
 }  // namespace cbfs
 

@@ -33,6 +33,12 @@ struct cbfs_labels_s {
     int64_t stride = 0;
     uint8_t* rows = nullptr;
     uint64_t* alls = nullptr;  // [cap]
+    // page-locked mirror of alls, the source of stream-ordered uploads: a
+    // range below the high-water mark of uploads not yet known to be done is
+    // rewritten only after alls_done (after cbfs_labels_reset)
+    uint64_t* h_alls = nullptr;
+    int64_t h_alls_hw = 0;
+    cudaEvent_t alls_done = nullptr;
     int* status = nullptr;
     int device = 0;
 };
@@ -417,22 +423,43 @@ void query_rows(const cbfs_labels_s* L, unsigned blocks, const int32_t* pairs, i
 #undef CBFS_QUERY
 }
 
+// Stream-ordered upload of the ALL words of clusters [L->count, L->count + C)
+// with sizes ks[c] (already checked) from the page-locked mirror.  A range
+// that an earlier upload may still be reading (after a reset) is rewritten
+// only once that upload has run.
+int put_alls(cbfs_labels_s* L, const int32_t* ks, int64_t ks_step, int C, cudaStream_t st) {
+    if (C == 0) return CBFS_OK;
+    if (L->count < L->h_alls_hw) {
+        if (cudaEventSynchronize(L->alls_done) != cudaSuccess) return CBFS_E_CUDA;
+        L->h_alls_hw = 0;
+    }
+    for (int c = 0; c < C; ++c) {
+        const int k = ks[(int64_t)c * ks_step];
+        L->h_alls[L->count + c] = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
+    }
+    if (cudaMemcpyAsync(L->alls + L->count, L->h_alls + L->count, sizeof(uint64_t) * C, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaEventRecord(L->alls_done, st) != cudaSuccess)
+        return CBFS_E_CUDA;
+    L->h_alls_hw = std::max<int64_t>(L->h_alls_hw, (int64_t)L->count + C);
+    return CBFS_OK;
+}
+
 }  // namespace
 
 namespace cbfs {
 
-int labels_reserve(cbfs_labels_s* L, int64_t n, int d, const int32_t* coff, int C, int* base) {
+int labels_reserve(cbfs_labels_s* L, int64_t n, int d, const int32_t* coff, int C, int* base, cudaStream_t st) {
     if (L->n != n || L->d != d || C < 0) return CBFS_E_INVALID;
     if (L->count + C > L->cap) return CBFS_E_NOMEM;
-    std::vector<uint64_t> alls((size_t)std::max(C, 1));
+    std::vector<int32_t> ks((size_t)std::max(C, 1));
     for (int c = 0; c < C; ++c) {
-        const int k = coff[c + 1] - coff[c];
-        if (k < 1 || k > 8 * L->wb) return CBFS_E_INVALID;
-        alls[c] = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
+        ks[c] = coff[c + 1] - coff[c];
+        if (ks[c] < 1 || ks[c] > 8 * L->wb) return CBFS_E_INVALID;
     }
     cudaSetDevice(L->device);
-    if (C > 0 && cudaMemcpy(L->alls + L->count, alls.data(), sizeof(uint64_t) * C, cudaMemcpyHostToDevice) != cudaSuccess)
-        return CBFS_E_CUDA;
+    const int rc = put_alls(L, ks.data(), 1, C, st);
+    if (rc) return rc;
     *base = L->count;
     L->count += C;
     return CBFS_OK;
@@ -476,6 +503,13 @@ int cbfs_labels_create_w(int64_t n, int C_capacity, int d, int w, size_t hbm_bud
         cbfs_labels_destroy(L);
         return CBFS_E_NOMEM;
     }
+    if (cudaMallocHost((void**)&L->h_alls, sizeof(uint64_t) * C_capacity) != cudaSuccess ||
+        cudaEventCreateWithFlags(&L->alls_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        L->h_alls = nullptr;
+        cbfs_labels_destroy(L);
+        return CBFS_E_NOMEM;
+    }
     if (cudaMemset(L->rows, 0, bytes) != cudaSuccess || cudaMemset(L->status, 0, sizeof(int)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess) {
         cbfs_labels_destroy(L);
@@ -491,11 +525,14 @@ int cbfs_labels_create(int64_t n, int C_capacity, int d, size_t hbm_budget_bytes
 
 int cbfs_labels_destroy(cbfs_labels_t L) {
     if (!L) return CBFS_OK;
+    status_forget(L);
     cudaSetDevice(L->device);
     cudaDeviceSynchronize();
     if (L->rows) cudaFree(L->rows);
     if (L->alls) cudaFree(L->alls);
     if (L->status) cudaFree(L->status);
+    if (L->h_alls) cudaFreeHost(L->h_alls);
+    if (L->alls_done) cudaEventDestroy(L->alls_done);
     delete L;
     return CBFS_OK;
 }
@@ -506,14 +543,10 @@ int cbfs_labels_append(cbfs_labels_t L, const uint8_t* dist, const uint64_t* mas
     if (L->count + C > L->cap) return CBFS_E_INVALID;
     if (C == 0) return CBFS_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<uint64_t> alls((size_t)C);
-    for (int c = 0; c < C; ++c) {
+    for (int c = 0; c < C; ++c)
         if (host_ks[c] < 1 || host_ks[c] > 8 * L->wb) return CBFS_E_INVALID;
-        alls[c] = host_ks[c] >= 64 ? ~0ull : ((1ull << host_ks[c]) - 1ull);
-    }
-    // synchronous copy of the small table: the host vector dies with the call
-    if (cudaMemcpy(L->alls + L->count, alls.data(), sizeof(uint64_t) * C, cudaMemcpyHostToDevice) != cudaSuccess)
-        return CBFS_E_CUDA;
+    const int rc = put_alls(L, host_ks, 1, C, st);
+    if (rc) return rc;
     if (L->n > 0) {
         append_rows(L, dist, masks, C, L->count, st);
         if (cudaGetLastError() != cudaSuccess) return CBFS_E_CUDA;
@@ -553,6 +586,7 @@ int cbfs_query_distance(cbfs_labels_t L, const int32_t* pairs, int64_t q, uint16
         default: query_rows<0>(L, (unsigned)blocks, pairs, q, out, st); break;
     }
     if (cudaGetLastError() != cudaSuccess) return CBFS_E_CUDA;
+    status_register(st, L->status, L);
     return CBFS_OK;
 }
 
@@ -591,7 +625,9 @@ int cbfs_query_local(cbfs_labels_t L, cbfs_graph_t g, const int32_t* pairs, int6
         }
 #undef CBFS_LOCAL
     }
-    return e == cudaSuccess ? CBFS_OK : CBFS_E_CUDA;
+    if (e != cudaSuccess) return CBFS_E_CUDA;
+    status_register(st, status, L ? (const void*)L : (const void*)g);
+    return CBFS_OK;
 }
 
 int cbfs_labels_status(cbfs_labels_t L, void* stream) {

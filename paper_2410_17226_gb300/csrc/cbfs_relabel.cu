@@ -122,9 +122,22 @@ namespace {
 // ---------------------------------------------------------------- rank order
 //
 // Ranks are produced on the device: a stable LSD radix sort of the key
-// 0xFFFFFFFF - deg(v) over the ids 0..n-1 (8-bit digits, only as many passes
-// as the largest degree has bits).  Ascending keys = descending degrees, and
-// stability keeps ascending ids within a degree.
+// 0xFFFFFFFF - order_deg(v) over the ids 0..n-1 (8-bit digits, only as many
+// passes as the largest degree has bits).  order_deg is the degree above
+// kPullSmall and the degree rounded up to a power of two at or below it, so
+// ascending keys give descending degrees down to kPullSmall, then the
+// buckets 32, 16, 8, 4, 2, 1 and finally the isolated vertices; stability
+// keeps ascending ids within a degree or a bucket.  The buckets keep most of
+// the input order of graphs whose vertices all have similar low degrees (a
+// road grid's row-major order, where a vertex's neighbours are the ids next
+// to it), while a warp's 32 consecutive vertices still differ in degree by
+// less than 2x.
+__device__ __forceinline__ uint32_t order_deg(int64_t dg) {
+    if (dg > kPullSmall || dg <= 1) return (uint32_t)dg;
+    uint32_t b = 2;
+    while ((int64_t)b < dg) b <<= 1;
+    return b;
+}
 
 constexpr int kSortItems = 16;                    // items per thread per tile
 constexpr int kSortTile = kThreads * kSortItems;  // 4096 items per CTA
@@ -154,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_degree_stats(int64_t n, int64_t nn
             keys[v] = 0;
             continue;
         }
-        keys[v] = 0xFFFFFFFFu - (uint32_t)dg;
+        keys[v] = 0xFFFFFFFFu - order_deg(dg);
         mx = dg > (int64_t)mx ? (unsigned long long)dg : mx;
         if (dg == 0) continue;
         if (dg <= kPullSmall) cls[0]++;
@@ -333,15 +346,15 @@ __global__ void k_rank_finish(int64_t n, const int32_t* perm, const int64_t* off
 }
 
 // The relabel kernels size their buffers by degree class, so the order is
-// checked before they run: perm and iperm are inverse permutations and the
-// degrees never increase along the ranks.
+// checked before they run: perm and iperm are inverse permutations and
+// order_deg never increases along the ranks.
 __global__ void k_check_rank(int64_t n, const int32_t* perm, const int32_t* iperm, const int64_t* deg_r,
                              DegreeStats* st) {
     bool bad = false;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = iperm[v];
         if (r < 0 || (int64_t)r >= n || perm[r] != (int32_t)v) bad = true;
-        if (v + 1 < n && deg_r[v] < deg_r[v + 1]) bad = true;
+        if (v + 1 < n && order_deg(deg_r[v]) < order_deg(deg_r[v + 1])) bad = true;
     }
     if (bad) atomicExch(&st->order_bad, 1ull);
 }
