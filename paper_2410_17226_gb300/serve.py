@@ -2,65 +2,76 @@
 
 The graph's labels stay resident on the GPU (``cbfs.Labels``, built from
 C-BFS outputs).  Requests -- arrays of vertex pairs of any size -- arrive at
-any time through ``submit`` and get a future.  A scheduler thread packs
-waiting requests, in arrival order, into batches of at most ``max_batch``
-pairs and launches each batch on one of ``slots`` CUDA streams as soon as a
-slot and its memory are free: pinned host staging -> H2D copy -> query kernel
-(``cbfs_query_distance``) -> D2H copy.  Batches launched while others are
-still on the GPU overlap with them (continuous batching, not a queue in front
-of one batch at a time).  A completion thread resolves the futures when a
-batch's event fires and records each request's latency from its arrival to
-its answer being on the host.
+any time through ``submit`` and get a ticket whose ``result()`` returns the
+answers.  Scheduling is native (``cbfs_server_*`` in libcbfs.so): a
+dispatcher thread packs waiting requests, in arrival order, into batches of
+at most ``max_batch`` pairs and launches each batch on one of ``slots`` CUDA
+streams as soon as a slot and its memory are free (page-locked staging -> H2D
+copy -> query kernel -> D2H copy); batches launched while others are still on
+the GPU overlap with them (continuous batching, not a queue in front of one
+batch at a time).  One waiter thread per stream completes requests as soon as
+their batch finishes, whatever the order batches were launched in.  Latency
+is measured natively, from ``submit`` to the answers being in host memory.
 
-Admission by memory: every in-flight batch holds ``pairs * 10`` bytes of
-device buffers (8 B pair + 2 B answer) from a budget of
-``memory_budget_bytes``; a batch starts only when its bytes fit.  Requests
-larger than ``max_batch`` are split over several batches and resolved when
-the last part is done.  The answers of a request do not depend on what else
-is in flight: every pair is answered independently by the same kernel.
+Admission by memory: the server's batch buffers (10 bytes per pair: int32
+pair + uint16 answer, ``slots * max_batch`` pairs) are allocated at start
+inside ``memory_budget_bytes`` (default: a quarter of the device memory free
+at that moment; ``max_batch`` shrinks to fit), and a batch is launched only
+when the bytes of the batches in flight plus its own fit that budget.
+Requests larger than ``max_batch`` are split over several batches and
+resolved when the last part is done.  The answers of a request do not depend
+on what else is in flight: every pair is answered independently by the same
+kernel.
 """
 from __future__ import annotations
 
-import collections
+import concurrent.futures
+import ctypes
 import gc
 import sys
 import threading
 import time
-from concurrent.futures import Future
 
 import numpy as np
 import torch
 
 from . import cbfs
 
-PAIR_BYTES = 8 + 2  # int32 pair + uint16 answer
 
+class Ticket:
+    """A submitted request; ``result()`` blocks until its answers are in."""
 
-class _Request:
-    __slots__ = ("pairs", "future", "t_arrival", "answers", "remaining", "t_done")
+    __slots__ = ("_server", "_id", "_pairs", "_out", "_done", "_exc", "_lock")
 
-    def __init__(self, pairs: np.ndarray, t_arrival: float):
-        self.pairs = pairs
-        self.future = Future()
-        self.t_arrival = t_arrival
-        self.answers = np.empty(pairs.shape[0], dtype=np.uint16)
-        self.remaining = pairs.shape[0]
-        self.t_done = None
+    def __init__(self, server: "QueryServer", ticket: int, pairs: np.ndarray, out: np.ndarray):
+        self._server, self._id, self._pairs, self._out = server, ticket, pairs, out
+        self._done, self._exc = False, None
+        self._lock = threading.Lock()
 
+    def _wait(self, timeout_s: float) -> bool:
+        with self._lock:
+            if self._done:
+                return True
+            rc = cbfs.lib().cbfs_server_wait(self._server._h, ctypes.c_uint64(self._id), float(timeout_s))
+            if rc == cbfs.E_TIMEOUT:
+                return False
+            self._done = True
+            self._pairs = None  # the server no longer reads it
+            if rc != cbfs.OK:
+                self._exc = cbfs.CbfsError(rc, "cbfs_server_wait")
+            self._server._forget(self._id)
+            return True
 
-class _Slot:
-    """One stream with its pinned staging and device buffers."""
+    def done(self) -> bool:
+        return self._wait(0.0)
 
-    def __init__(self, max_batch: int, device):
-        self.stream = torch.cuda.Stream(device=device)
-        self.h_pairs = cbfs.pinned_empty((max_batch, 2), torch.int32)
-        self.h_out = cbfs.pinned_empty(max_batch, torch.int16)
-        self.d_pairs = torch.empty((max_batch, 2), dtype=torch.int32, device=device)
-        self.d_out = torch.empty(max_batch, dtype=torch.int16, device=device)
-        self.event = torch.cuda.Event()
-        self.parts = []  # (request, offset in request, offset in batch, count)
-        self.count = 0
-        self.bytes = 0
+    def result(self, timeout: float | None = None) -> np.ndarray:
+        """uint16 [q] answers (0xFFFF: no common landmark)."""
+        if not self._wait(-1.0 if timeout is None else timeout):
+            raise concurrent.futures.TimeoutError()
+        if self._exc is not None:
+            raise self._exc
+        return self._out
 
 
 class QueryServer:
@@ -68,60 +79,56 @@ class QueryServer:
                  memory_budget_bytes: int | None = None, device=None, pause_gc: bool = False,
                  switch_interval_s: float | None = None):
         """``pause_gc`` disables Python's cyclic garbage collector while the
-        server runs (its pauses over many live requests were the latency
-        tail); ``switch_interval_s`` shortens the interpreter's thread switch
-        interval so the scheduler and completion threads do not wait 5 ms
-        turns.  Both are process-wide settings, restored by ``close``."""
+        server runs and ``switch_interval_s`` shortens the interpreter's
+        thread switch interval: both only help the Python clients that submit
+        and wait (scheduling itself is native).  Both are process-wide
+        settings, restored by ``close``."""
+        if device is not None and torch.device(device).index not in (None, torch.cuda.current_device()):
+            raise ValueError("the server runs on the current CUDA device")
         self._gc_was_enabled = gc.isenabled()
         self._old_switch = sys.getswitchinterval()
         self._pause_gc = pause_gc
+        self.labels = labels
+        self._h = ctypes.c_void_p()
+        cbfs._check(cbfs.lib().cbfs_server_create(labels._h, int(max_batch), int(slots),
+                                                  int(memory_budget_bytes or 0), ctypes.byref(self._h)),
+                    "cbfs_server_create")
         if pause_gc:
             gc.disable()
         if switch_interval_s:
             sys.setswitchinterval(switch_interval_s)
-        self.labels = labels
-        self.max_batch = int(max_batch)
-        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
-        self.budget = int(memory_budget_bytes) if memory_budget_bytes else slots * self.max_batch * PAIR_BYTES
-        if self.budget < PAIR_BYTES:
-            raise ValueError("memory budget below one pair")
-        self._free_slots = collections.deque(_Slot(self.max_batch, self.device) for _ in range(slots))
-        self._inflight = collections.deque()
-        self._pending = collections.deque()  # [request, offset]
-        self._used = 0
-        self._cv = threading.Condition()
-        self._stop = False
-        self.latencies_ms = []
-        self.batches = 0
-        self.pairs_done = 0
-        self.errors = []
-        self._sched = threading.Thread(target=self._schedule, name="cbfs-serve-sched", daemon=True)
-        self._compl = threading.Thread(target=self._complete, name="cbfs-serve-done", daemon=True)
-        self._sched.start()
-        self._compl.start()
+        self._open = {}  # ticket id -> Ticket not yet waited for
+        self._mu = threading.Lock()
+        c = self._counts()
+        self.max_batch, self.budget = int(c[3]), int(c[4])
 
     # ----------------------------------------------------------------- API
-    def submit(self, pairs) -> Future:
-        """Queue a request (int32 [q, 2] vertex pairs); the future yields uint16 [q]."""
+    def submit(self, pairs) -> Ticket:
+        """Queue a request (int32 [q, 2] vertex pairs); ``result()`` yields uint16 [q]."""
         p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
-        req = _Request(p, time.perf_counter())
-        if p.shape[0] == 0:
-            req.t_done = req.t_arrival
-            req.future.set_result(req.answers)
-            return req.future
-        with self._cv:
-            if self._stop:
-                raise RuntimeError("server closed")
-            self._pending.append([req, 0])
-            self._cv.notify_all()
-        return req.future
+        out = np.empty(p.shape[0], dtype=np.uint16)
+        tid = ctypes.c_uint64()
+        cbfs._check(cbfs.lib().cbfs_server_submit(self._h, p.ctypes.data if p.size else None, int(p.shape[0]),
+                                                  out.ctypes.data if p.size else None, ctypes.byref(tid)),
+                    "cbfs_server_submit")
+        t = Ticket(self, tid.value, p, out)
+        with self._mu:
+            self._open[tid.value] = t
+        return t
+
+    def _forget(self, tid: int):
+        with self._mu:
+            self._open.pop(tid, None)
 
     def close(self):
-        with self._cv:
-            self._stop = True
-            self._cv.notify_all()
-        self._sched.join()
-        self._compl.join()
+        if not self._h.value:
+            return
+        with self._mu:
+            left = list(self._open.values())
+        for t in left:  # every request is answered before the server goes
+            t._wait(-1.0)
+        cbfs.lib().cbfs_server_destroy(self._h)
+        self._h = ctypes.c_void_p()
         sys.setswitchinterval(self._old_switch)
         if self._pause_gc and self._gc_was_enabled:
             gc.enable()
@@ -132,102 +139,37 @@ class QueryServer:
     def __exit__(self, *exc):
         self.close()
 
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _counts(self):
+        c = (ctypes.c_uint64 * 5)()
+        cbfs._check(cbfs.lib().cbfs_server_stats(self._h, c, None, 0, None), "cbfs_server_stats")
+        return list(c)
+
     def stats(self) -> dict:
-        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        return {"requests": len(self.latencies_ms), "batches": self.batches, "pairs": self.pairs_done,
+        """Completed requests, batches, pairs answered and the latency
+        percentiles (ms, arrival to answers on the host)."""
+        n = ctypes.c_int64()
+        cbfs._check(cbfs.lib().cbfs_server_stats(self._h, None, None, 0, ctypes.byref(n)), "cbfs_server_stats")
+        lat = np.zeros(max(n.value, 1), dtype=np.float64)
+        c = (ctypes.c_uint64 * 5)()
+        cbfs._check(cbfs.lib().cbfs_server_stats(self._h, c, lat.ctypes.data, lat.size, ctypes.byref(n)),
+                    "cbfs_server_stats")
+        lat = lat[:max(min(n.value, lat.size), 1)]
+        return {"requests": int(c[0]), "batches": int(c[1]), "pairs": int(c[2]),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean())}
-
-    # ------------------------------------------------------------ threads
-    def _schedule(self):
-        while True:
-            with self._cv:
-                while True:
-                    if self._stop and not self._pending:
-                        self._cv.notify_all()
-                        return
-                    if self._pending and self._free_slots and self._used + PAIR_BYTES <= self.budget:
-                        break
-                    self._cv.wait()
-                slot = self._free_slots.popleft()
-                # pack waiting requests in arrival order until the batch or the budget is full
-                room = min(self.max_batch, (self.budget - self._used) // PAIR_BYTES)
-                slot.parts, slot.count = [], 0
-                while self._pending and slot.count < room:
-                    item = self._pending[0]
-                    req, off = item
-                    take = min(req.pairs.shape[0] - off, room - slot.count)
-                    slot.parts.append((req, off, slot.count, take))
-                    slot.count += take
-                    if off + take == req.pairs.shape[0]:
-                        self._pending.popleft()
-                    else:
-                        item[1] = off + take
-                slot.bytes = slot.count * PAIR_BYTES
-                self._used += slot.bytes
-            try:
-                self._launch(slot)
-            except Exception as exc:  # surface kernel/launch failures on the futures
-                self.errors.append(exc)
-                for req, _, _, _ in slot.parts:
-                    if not req.future.done():
-                        req.future.set_exception(exc)
-                with self._cv:
-                    self._used -= slot.bytes
-                    self._free_slots.append(slot)
-                    self._cv.notify_all()
-                continue
-            with self._cv:
-                self._inflight.append(slot)
-                self._cv.notify_all()
-
-    def _launch(self, slot: _Slot):
-        hp = slot.h_pairs.numpy()
-        for req, off, pos, cnt in slot.parts:
-            hp[pos:pos + cnt] = req.pairs[off:off + cnt]
-        q = slot.count
-        with torch.cuda.stream(slot.stream):
-            slot.d_pairs[:q].copy_(slot.h_pairs[:q], non_blocking=True)
-            self.labels.query(slot.d_pairs[:q], out=slot.d_out[:q], stream=slot.stream)
-            slot.h_out[:q].copy_(slot.d_out[:q], non_blocking=True)
-            slot.event.record(slot.stream)
-
-    def _complete(self):
-        while True:
-            with self._cv:
-                while not self._inflight:
-                    if self._stop and not self._pending and not self._sched.is_alive():
-                        return
-                    self._cv.wait(timeout=0.05)
-                slot = self._inflight[0]
-            slot.event.synchronize()
-            now = time.perf_counter()
-            ho = slot.h_out.numpy().view(np.uint16)
-            finished = []
-            for req, off, pos, cnt in slot.parts:
-                req.answers[off:off + cnt] = ho[pos:pos + cnt]
-                req.remaining -= cnt
-                if req.remaining == 0:
-                    req.t_done = now
-                    finished.append(req)
-            with self._cv:
-                self._inflight.popleft()
-                self._used -= slot.bytes
-                self.batches += 1
-                self.pairs_done += slot.count
-                for req in finished:
-                    self.latencies_ms.append((req.t_done - req.t_arrival) * 1e3)
-                self._free_slots.append(slot)
-                self._cv.notify_all()
-            for req in finished:
-                req.future.set_result(req.answers)
+                "mean_ms": float(lat.mean()), "max_batch": int(c[3]), "budget_bytes": int(c[4])}
 
 
 def poisson_load(server: QueryServer, n: int, rate_rps: float, duration_s: float, max_pairs: int, seed: int):
     """Offers requests with exponential inter-arrival times (rate_rps per
     second) and sizes uniform in 1..max_pairs for duration_s seconds; each
     request is a slice of a pregenerated pool of uniform random pairs, so the
-    client itself is not the bottleneck.  Returns (futures, pairs offered,
+    client itself is not the bottleneck.  Returns (tickets, pairs offered,
     elapsed seconds)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     pool = rng.integers(0, n, size=(4 * max_pairs, 2), dtype=np.int64).astype(np.int32)
