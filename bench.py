@@ -98,6 +98,13 @@ def job_value(units_per_rank: int, ranks: int, t_max_ms: float) -> float:
     return units_per_rank * ranks / (t_max_ms / 1e3) / 1e9
 
 
+def bench_config(scale: int, C: int, d: int, n: int, nnz: int, sources: int, query_batch: int) -> dict:
+    """The workload's description, the same in both arms' lines."""
+    return {"workload": workload_text(scale, C), "graph": f"rmat-s{scale}-ef16", "n": int(n), "nnz": int(nnz),
+            "clusters": int(C), "sources": int(sources), "d": int(d), "query_batch": int(query_batch),
+            "l2": "inputs larger than L2 (0.5 GB CSR, 18 GB outputs, 18 GB labels)"}
+
+
 def workload(scale: int, C: int, rank: int):
     off, adj = I.rmat(scale)
     clusters, d = I.star_clusters(off, adj, C, seed=rank_seed(rank), size="uniform")
@@ -299,8 +306,8 @@ def bfs_comparison(g, off, adj, seed: int, seq=None):
     k = statistics.mean(len(S) for S in clusters)
     out = {"clusters": len(clusters), "mean_sources": round(k, 1), "d": d,
            "cbfs_ms_per_cluster": round(cb, 3),
-           "bfs_per_source_ms_one_per_wave": round(bf, 3),
-           "bfs_per_source_ms_eight_per_wave": round(b8, 3),
+           "bfs_all_k_sources_ms_one_per_wave": round(bf, 3),
+           "bfs_all_k_sources_ms_eight_per_wave": round(b8, 3),
            "bit_level_gain": round(bf / cb, 2),
            "bfs_gteps_one_per_wave": round(k * comp_edges / (bf / 1e3) / 1e9, 3),
            "cbfs_gteps": round(k * comp_edges / (cb / 1e3) / 1e9, 3)}
@@ -465,44 +472,67 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
         alg = ARC_BYTES * A + VERTEX_BYTES * V + count * n * (1 + 8 * d)
         del dist, masks
         torch.cuda.empty_cache()
+    peak, _ = measured_peak_hbm()
     return {"graph": f"road grid {side}x{side}, 10% deleted, 1% shortcuts", "n": int(n), "nnz": int(adj.size),
             "clusters": count, "d": d, "per_launch": per_launch, "ms_all_clusters": round(total_ms, 2),
             "gteps": round(src_edges / (total_ms / 1e3) / 1e9, 2), "max_rounds": rounds,
-            "alg_gbs": round(alg / (total_ms / 1e3) / 1e9, 1)}
+            "arcs_per_s": round(A / (total_ms / 1e3), 1),
+            "alg_gbs": round(alg / (total_ms / 1e3) / 1e9, 1), "alg_frac": round(alg / (total_ms / 1e3) / 1e9 / peak, 4)}
 
 
-def single_cluster_config(cbfs, reps: int = 50):
-    """Single C-BFS, plain form: R-MAT scale 14, one cluster of a seeded
-    random vertex and up to 63 of its neighbours, d = 2 (its state fits L2:
-    time and GTEPS, no HBM roofline)."""
+def single_cluster_config(cbfs, reps: int = 20):
+    """Single C-BFS, plain form: R-MAT scale 14, clusters of a seeded random
+    vertex and up to 63 of its neighbours, d = 2 (the state fits L2: time and
+    GTEPS, no HBM roofline).  Ten seeded clusters with uniform random centres
+    (most centres have few neighbours, so k is small) and ten whose centres
+    have degree >= 63 (k = 64); per cluster the device time of a call
+    (stream-ordered calls back to back, CUDA events) and the host latency of
+    a blocking call."""
     import torch
 
     off, adj = I.rmat(14)
-    clusters, d = I.star_clusters(off, adj, 1, seed=I.MASTER_SEED, size="max")
-    S = clusters[0]
     deg = np.diff(off)
+    out = {"graph": "R-MAT scale 14", "d": 2}
     with cbfs.Graph(off, adj) as g:
         dist = torch.empty(g.n, dtype=torch.uint8, device="cuda")
-        masks = torch.empty((d, g.n), dtype=torch.int64, device="cuda")
-        for _ in range(3):
-            g.run(S, d, dist, masks)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            g.run(S, d, dist, masks)
-        torch.cuda.synchronize()
-        ms = (time.perf_counter() - t0) * 1e3 / reps
-        reached = dist.cpu().numpy() != 255
-    edges = len(S) * int(deg[reached].sum()) // 2
-    return {"graph": "R-MAT scale 14", "sources": len(S), "d": d, "ms_per_call": round(ms, 4),
-            "gteps": round(edges / (ms / 1e3) / 1e9, 2), "mode": "cbfs_run, call to call (host wall, synchronised)"}
+        masks = torch.empty((2, g.n), dtype=torch.int64, device="cuda")
+        stream = torch.cuda.current_stream()
+        for name, kw in (("random_centres", {}), ("centres_deg_ge_63", {"min_deg": 63})):
+            clusters, d = I.star_clusters(off, adj, 10, seed=I.MASTER_SEED, size="max", **kw)
+            edges = 0
+            for S in clusters:  # warm-up (records each call shape's graph) and the reached edges
+                g.run(S, d, dist, masks)
+                edges += len(S) * int(deg[dist.cpu().numpy() != 255].sum()) // 2
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                for S in clusters:
+                    g.run(S, d, dist, masks, check=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if cbfs.sync_status(stream) != cbfs.OK:
+                raise RuntimeError("single-cluster calls reported an error")
+            dev_ms = e0.elapsed_time(e1) / (reps * len(clusters))
+            lat = []
+            for _ in range(3):
+                for S in clusters:
+                    t0 = time.perf_counter()
+                    g.run(S, d, dist, masks)  # blocking: waits for the stream and checks the status
+                    lat.append((time.perf_counter() - t0) * 1e3)
+            out[name] = {"clusters": len(clusters), "mean_sources": round(statistics.mean(len(S) for S in clusters), 1),
+                         "ms_per_call_device": round(dev_ms, 4), "ms_per_call_host_p50": round(statistics.median(lat), 4),
+                         "gteps": round(edges / len(clusters) / (dev_ms / 1e3) / 1e9, 2)}
+    return out
 
 
 def label_construction_config(cbfs, budget_bytes_per_vertex: int = 1024, count: int = 1024, per_launch: int = 32):
     """Label construction at scale: R-MAT scale 24 (int64 offsets), 1024
     degree-ordered clusters of 64 (Section 4.2 selection), 32 per launch, the
     labels that fit 1024 B/vertex kept on the device (the rest computed and
-    dropped).  Reports the traversal rate over all 1024 clusters."""
+    dropped).  Reports the traversal rate over all 1024 clusters: source-edge
+    GTEPS, arcs scanned per second (Sigma A / t) and the algorithmic-byte
+    rate, from CUDA events around each launch."""
     import torch
 
     t_gen = time.perf_counter()
@@ -517,28 +547,43 @@ def label_construction_config(cbfs, budget_bytes_per_vertex: int = 1024, count: 
         dist = torch.empty((per_launch, n), dtype=torch.uint8, device="cuda")
         masks = torch.empty((per_launch, d, n), dtype=torch.int64, device="cuda")
         g.run_batched(clusters[:per_launch], d, dist, masks)  # warm-up
-        kept, src_edges = 0, 0
+        stream = torch.cuda.current_stream()
+        kept, A, V, trav_ms = 0, 0, 0, 0.0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for b in range(0, len(clusters), per_launch):
             part = clusters[b:b + per_launch]
             k = len(part)
-            g.run_batched(part, d, dist[:k], masks[:k])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.run_batched(part, d, dist[:k], masks[:k], check=False)
+            e1.record(stream)
             take = min(k, int(cap) - kept)
             if take > 0:
                 L.append(dist[:take], masks[:take], [len(S) for S in part[:take]])
                 kept += take
+            e1.synchronize()
+            trav_ms += e0.elapsed_time(e1)
+            st = g.output_stats(dist[:k], masks[:k], [len(S) for S in part], d)  # untimed: outside the events
+            A += int(st[:, 1].sum())
+            V += int(st[:, 0].sum())
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t0) * 1e3
+        if cbfs.sync_status(stream) != cbfs.OK:
+            raise RuntimeError("label construction reported an error")
         reached = dist[0].cpu().numpy() != 255  # the degree clusters all sit in the giant component
         comp_edges = int(deg[reached].sum()) // 2
         src_edges = sum(len(S) for S in clusters) * comp_edges
         del dist, masks, L
         torch.cuda.empty_cache()
+    alg = ARC_BYTES * A + VERTEX_BYTES * V + len(clusters) * n * (1 + 8 * d)
+    peak, _ = measured_peak_hbm()
     return {"graph": "R-MAT scale 24 (int64 offsets)", "n": int(n), "nnz": int(adj.size), "clusters": len(clusters),
             "per_launch": per_launch, "labels_kept": int(kept), "label_budget_bytes_per_vertex": budget_bytes_per_vertex,
-            "ms_all_clusters": round(ms, 1), "gteps": round(src_edges / (ms / 1e3) / 1e9, 1),
-            "graph_generation_s": round(gen_s, 1)}
+            "ms_all_clusters": round(ms, 1), "traversal_ms": round(trav_ms, 1),
+            "gteps": round(src_edges / (trav_ms / 1e3) / 1e9, 1),
+            "arcs_per_s": round(A / (trav_ms / 1e3), 1), "alg_gbs": round(alg / (trav_ms / 1e3) / 1e9, 1),
+            "alg_frac": round(alg / (trav_ms / 1e3) / 1e9 / peak, 4), "graph_generation_s": round(gen_s, 1)}
 
 
 # ---------------------------------------------------------------- arms
@@ -563,8 +608,8 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall_total / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": workload_text(args.scale, args.clusters), "graph": f"rmat-s{args.scale}-ef16",
-                   "clusters": args.clusters, "d": d},
+        "config": bench_config(args.scale, len(clusters), d, off.size - 1, adj.size, sum(len(S) for S in clusters),
+                               args.query_batch),
         "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                          "sample": f"each step: 16 of the {len(clusters)} clusters, Algorithm 1 in plain C, "
                                    "one cluster per core"},
@@ -641,7 +686,8 @@ def run_cbfs(args, ws, rank, local):
     coff = np.concatenate([[0], np.cumsum(ks)]).astype(np.int32)
 
     def step(ev=None):
-        g.run_batched(None, d, dist, masks, tune=tset, sources_concat=src_cat, cluster_off=coff)
+        # stream-ordered: the step enqueues its work; errors are read once after the timed region
+        g.run_batched(None, d, dist, masks, tune=tset, sources_concat=src_cat, cluster_off=coff, check=False)
         if ev is not None:
             ev.record(stream)
         L.reset()
@@ -665,6 +711,9 @@ def run_cbfs(args, ws, rank, local):
         t_end.record(stream)
         torch.cuda.synchronize()
     barrier()
+    st_rc = cbfs.sync_status(stream)
+    if st_rc != cbfs.OK:
+        raise cbfs.CbfsError(st_rc, "timed steps")
     prof = g.profile(False)  # launch counts of the timed steps
     t_ms = t_start.elapsed_time(t_end)
     cbfs_ms = sum(a.elapsed_time(b) for a, b in marks)
@@ -684,7 +733,13 @@ def run_cbfs(args, ws, rank, local):
     roofline = {"kernel": f"cbfs_run_batched traversal graph (vertex + edge phases of all {C} clusters)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "avg_launch_ms": round(cbfs_step_ms, 3), "alg_bytes_per_launch": int(alg_bytes_step)}
+                "avg_launch_ms": round(cbfs_step_ms, 3), "alg_bytes_per_launch": int(alg_bytes_step),
+                # Sigma A_c / t: arcs scanned in the push model (Theorem 1) per second, all clusters
+                "arcs_per_s": round(A / (cbfs_step_ms / 1e3), 1)}
+    if traffic:
+        # the physical side: ncu DRAM bytes of the same launch over the same time
+        roofline["physical_gbs"] = round(traffic / (cbfs_step_ms / 1e3) / 1e9, 1)
+        roofline["physical_frac"] = round(traffic / (cbfs_step_ms / 1e3) / 1e9 / peak, 4)
     # per-kernel split from one extra, untimed traversal with event brackets (host-driven rounds)
     g.profile(True)
     g.run_batched(None, d, dist, masks, tune=dict(tset, host_loop=1), sources_concat=src_cat, cluster_off=coff)
@@ -884,11 +939,8 @@ def run_cbfs(args, ws, rank, local):
             "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": workload_text(args.scale, C), "graph": f"rmat-s{args.scale}-ef16", "n": n,
-                       "nnz": int(adj.size),
-                       "clusters": C, "sources": int(ks.sum()), "d": d, "tune": tset,
-                       "tune_cached": tn.get("cached"), "query_batch": args.query_batch,
-                       "l2": "inputs larger than L2 (0.5 GB CSR, 18 GB outputs, 18 GB labels)"},
+            "config": bench_config(args.scale, C, d, n, adj.size, int(ks.sum()), args.query_batch),
+            "tune": dict(tset, cached=tn.get("cached")),
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -905,10 +957,51 @@ def run_cbfs(args, ws, rank, local):
             "next": nxt,
             "configs": configs,
         }
+        # last, so that it stays inside the tail of the output a reader keeps
+        line["summary"] = summary_of(line)
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def summary_of(line: dict) -> dict:
+    """The figures of every workload in a few hundred bytes."""
+    def get(*path):
+        x = line
+        for k in path:
+            if not isinstance(x, dict) or k not in x:
+                return None
+            x = x[k]
+        return x
+
+    rf = line["roofline"]
+    out = {"gteps": line["value"], "ms_per_step": line["ms_per_step"],
+           "traversal_ms": rf["avg_launch_ms"], "alg_frac": rf["frac"],
+           "physical_frac": rf.get("physical_frac"), "garcs_per_s": round(rf["arcs_per_s"] / 1e9, 1),
+           "e2e_gteps": get("e2e", "value"),
+           "batched_speedup_vs_one_cluster_per_launch": get("one_cluster_per_launch", "batched_speedup"),
+           "query_kernel_frac": get("query", "kernel", "frac"),
+           "query_single_p50_p99_ms": [get("query", "p50_ms"), get("query", "p99_ms")],
+           "serving_saturation_qps": get("serving", "saturation_qps")}
+    for load in ("0.5x", "0.8x"):
+        out[f"serving_{load}_p50_p99_ms"] = [get("serving", "offered", load, "p50_ms"),
+                                             get("serving", "offered", load, "p99_ms")]
+    rg = get("next", "road_grid")
+    if rg:
+        out["road_grid_4096"] = {"gteps": rg["gteps"], "alg_frac": rg["alg_frac"], "ms": rg["ms_all_clusters"],
+                                 "garcs_per_s": round(rg["arcs_per_s"] / 1e9, 1)}
+    lc = get("configs", "label_construction_s24")
+    if lc:
+        out["labels_s24_1024"] = {"traversal_ms": lc["traversal_ms"], "alg_frac": lc["alg_frac"],
+                                  "garcs_per_s": round(lc["arcs_per_s"] / 1e9, 1)}
+    sc = get("configs", "single_cluster_s14")
+    if sc:
+        out["single_s14_ms"] = {k: sc[k]["ms_per_call_device"] for k in ("random_centres", "centres_deg_ge_63")}
+    bc = get("next", "bfs_comparison")
+    if bc:
+        out["bit_level_gain"] = bc["bit_level_gain"]
+    return out
 
 
 def record_traffic(csv_path: str, clusters: int, note: str):

@@ -33,3 +33,30 @@ def test_traffic_from_csv(tmp_path):
     assert out["per_kernel_bytes"]["cbfs::k_phase_a<4>"] == int(150e6)
     assert "k_validate" not in " ".join(out["per_kernel_bytes"])
     assert out["source_hash"] == bench.kernel_source_hash() and len(out["source_hash"]) == 16
+
+
+def test_summary_of_a_line_keeps_every_workload():
+    line = {"value": 1000.0, "ms_per_step": 150.0,
+            "roofline": {"avg_launch_ms": 140.0, "frac": 1.0, "arcs_per_s": 5e11, "physical_frac": 0.3},
+            "e2e": {"value": 900.0},
+            "one_cluster_per_launch": {"batched_speedup": 2.3},
+            "query": {"p50_ms": 0.1, "p99_ms": 0.2, "kernel": {"frac": 0.8}},
+            "serving": {"saturation_qps": 7e8, "offered": {"0.5x": {"p50_ms": 0.4, "p99_ms": 0.7},
+                                                           "0.8x": {"p50_ms": 0.8, "p99_ms": 2.0}}},
+            "next": {"road_grid": {"gteps": 160.0, "alg_frac": 0.2, "ms_all_clusters": 770.0, "arcs_per_s": 2e11},
+                     "bfs_comparison": {"bit_level_gain": 28.0}},
+            "configs": {"label_construction_s24": {"traversal_ms": 1200.0, "alg_frac": 0.5, "arcs_per_s": 3e11},
+                        "single_cluster_s14": {"random_centres": {"ms_per_call_device": 0.05},
+                                               "centres_deg_ge_63": {"ms_per_call_device": 0.08}}}}
+    s = bench.summary_of(line)
+    assert s["garcs_per_s"] == 500.0 and s["physical_frac"] == 0.3
+    assert s["batched_speedup_vs_one_cluster_per_launch"] == 2.3
+    assert s["serving_0.8x_p50_p99_ms"] == [0.8, 2.0]
+    assert s["road_grid_4096"]["alg_frac"] == 0.2 and s["labels_s24_1024"]["garcs_per_s"] == 300.0
+    assert s["single_s14_ms"]["centres_deg_ge_63"] == 0.08 and s["bit_level_gain"] == 28.0
+    # missing sections (a run with --no-next) leave their keys out or None
+    short = {k: line[k] for k in ("value", "ms_per_step", "roofline")}
+    s2 = bench.summary_of(short)
+    assert s2["serving_0.5x_p50_p99_ms"] == [None, None] and "road_grid_4096" not in s2
+    import json
+    assert len(json.dumps(s)) < 1200
