@@ -1884,6 +1884,8 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     if (!rc) rc = dev_alloc(&g->off_r, n + 1);
     if (!rc) rc = dev_alloc(&g->adj_r, nnz);
     if (rc) return fail(rc);
+    // the status word is sticky across calls: it starts at CBFS_OK and only a read clears it
+    if (cudaMemsetAsync(g->status, 0, sizeof(int), st) != cudaSuccess) return fail(CBFS_E_CUDA);
     if (cudaMallocHost((void**)&g->h_q, sizeof(unsigned long long) * (kMaxRounds + 2)) != cudaSuccess) {
         g->h_q = nullptr;
         return fail(CBFS_E_NOMEM);
