@@ -62,8 +62,10 @@ def test_noalloc_equals_oracle_and_allocating_entry_point_on_two_calls(cb):
 def test_noalloc_at_its_size_limits(cb):
     """n = 131,072 vertices (the limit) and 3.7 M arcs (89 % of the arc
     limit), 154 hubs whose lists exceed 2048 arcs (cut into pieces), 64-source
-    stars (one centred on a hub); then a grid of exactly 131,072 vertices
-    with d = 15 (the largest bound) and a 64-vertex ball, and k = 1, d = 0."""
+    stars (one centred on a hub) and k = 1, d = 0; then a 362 x 362 road
+    grid (131,044 vertices; its shortcuts keep every distance below 255, which
+    a plain grid of that size would exceed) with a 64-vertex ball and d = 15,
+    the largest bound."""
     off, adj = I.rmat(17)
     n = off.size - 1
     assert n == MAX_N and MAX_NNZ * 0.85 < adj.size <= MAX_NNZ
@@ -77,8 +79,8 @@ def test_noalloc_at_its_size_limits(cb):
         _equals_oracle_and_cbfs_run(cb, g, off, adj, off_d, adj_d, S, d)
     _equals_oracle_and_cbfs_run(cb, g, off, adj, off_d, adj_d, clusters[1][:1], 0)
 
-    goff, gadj = I.grid(256, 512)
-    assert goff.size - 1 == MAX_N
+    goff, gadj = I.road_grid(362)
+    assert MAX_N - 100 < goff.size - 1 <= MAX_N
     gg = cb.Graph(goff, gadj)
     balls, _ = I.ball_clusters(goff, gadj, 1, 64, seed=I.MASTER_SEED + 78)
     _equals_oracle_and_cbfs_run(cb, gg, goff, gadj, torch.from_numpy(goff).cuda(), torch.from_numpy(gadj).cuda(),
