@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--no-configs", dest="configs", action="store_false",
                     help="skip timing the single-cluster (scale 14) and label-construction (scale 24) workloads")
     ap.add_argument("--record-traffic", default="",
-                    help="ncu CSV (dram__bytes_read/write.sum of the traversal kernels of `runcli --host-loop`) "
-                         "to turn into profiles/traffic.json for the current kernel sources, then exit")
-    ap.add_argument("--traffic-clusters", type=int, default=16, help="clusters of the captured run")
+                    help="comma-separated ncu CSVs (dram__bytes_read/write.sum of the traversal kernels of one "
+                         "`runcli --host-loop` call) to turn into profiles/traffic.json for the current kernel "
+                         "sources, then exit")
+    ap.add_argument("--traffic-run", default="", help="the runcli output line of the captured call")
     return ap.parse_args()
 
 
@@ -228,9 +229,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, or None when the
-    kernels changed since it was taken."""
+def ncu_traffic(kernel: str, alg_bytes: int):
+    """DRAM bytes of a launch of `alg_bytes` algorithmic bytes, from the
+    committed ncu record (physical bytes per algorithmic byte of a captured
+    wave), or None when the kernels changed since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -238,9 +240,9 @@ def ncu_traffic(kernel: str):
     except (OSError, ValueError):
         return None
     e = t.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash() or "dram_bytes_per_alg_byte" not in e:
         return None
-    return e.get("dram_bytes_per_launch")
+    return int(e["dram_bytes_per_alg_byte"] * alg_bytes)
 
 
 # ------------------------------------------------- single-source BFS and d
@@ -729,7 +731,7 @@ def run_cbfs(args, ws, rank, local):
     # traversal kernel of the call), timed by events around it in every step
     cbfs_step_ms = cbfs_ms / args.steps
     achieved = alg_bytes_step / (cbfs_step_ms / 1e3) / 1e9
-    traffic = ncu_traffic("traversal")
+    traffic = ncu_traffic("traversal", alg_bytes_step)
     roofline = {"kernel": f"cbfs_run_batched traversal graph (vertex + edge phases of all {C} clusters)",
                 "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
@@ -1004,52 +1006,76 @@ def summary_of(line: dict) -> dict:
     return out
 
 
-def record_traffic(csv_path: str, clusters: int, note: str):
-    """Writes profiles/traffic.json from an ncu CSV (see traffic_from_csv)."""
-    out = traffic_from_csv(csv_path, clusters, note)
+def record_traffic(csv_paths: str, run_json: str, note: str):
+    """Writes profiles/traffic.json from ncu CSVs and the runcli line of the
+    captured run (see traffic_from_csv)."""
+    with open(run_json) as f:
+        run = json.loads([ln for ln in f.read().splitlines() if ln.startswith("{")][-1])
+    out = traffic_from_csv(csv_paths.split(","), run, note)
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps(out))
     return 0
 
 
-def traffic_from_csv(csv_path: str, clusters: int, note: str) -> dict:
-    """DRAM bytes per cluster of the traversal kernels, from an ncu CSV of
-    one host-driven `runcli` call, scaled to the bench's 256-cluster launch
-    (traffic grows with the clusters at a fixed graph)."""
+def memset_bytes_per_wave(n: int, P: int) -> int:
+    """Bytes the per-wave state resets write: vis and acc (8 P bytes per
+    vertex each), the claim stamps (4), the Delta rows (P), two frontier
+    bitmaps and the round control blocks (288 x 56 bytes)."""
+    bitmap_words = (n + 31) // 32 + 1
+    return (16 * P + 4 + P) * n + 2 * 4 * bitmap_words + 288 * 56
+
+
+def traffic_from_csv(csv_paths, run: dict, note: str) -> dict:
+    """DRAM bytes of the traversal kernels of one host-driven `runcli` call
+    (ncu dram__bytes_read.sum + dram__bytes_write.sum, one kernel and at most
+    three launches per capture, the captures together covering every launch
+    of the call), plus the per-wave memset bytes counted from their sizes,
+    over that call's algorithmic bytes (13 A + 41 V + C n (1 + 8 d)).  The
+    bench multiplies its own launch's algorithmic bytes by this ratio."""
     import csv as csv_
 
     kinds = ("k_seed", "k_phase_a", "k_phase_b", "k_emit", "k_check_sources", "k_map_seeds")
-    total = 0.0
-    per_kernel = {}
-    with open(csv_path) as f:
-        rows = [r for r in csv_.reader(f)]
-    hdr = next(i for i, r in enumerate(rows) if r and r[0] == "ID")
-    cols = rows[hdr]
-    for r in rows[hdr + 1:]:
-        if len(r) != len(cols):
+    per_kernel, launches = {}, {}
+    for path in csv_paths:
+        with open(path) as f:
+            rows = [r for r in csv_.reader(f)]
+        hdr = next((i for i, r in enumerate(rows) if r and r[0] == "ID"), None)
+        if hdr is None:
             continue
-        rec = dict(zip(cols, r))
-        name = rec["Kernel Name"]
-        if not rec["Metric Name"].startswith("dram__bytes") or not any(k in name for k in kinds):
-            continue
-        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[rec["Metric Unit"]]
-        v = float(rec["Metric Value"].replace(",", "")) * scale
-        key = name.split("(")[0].replace("void ", "")
-        per_kernel[key] = per_kernel.get(key, 0.0) + v
-        total += v
-    per_cluster = total / clusters
-    return {"traversal": {"dram_bytes_per_launch": int(per_cluster * 256), "per_cluster_bytes": int(per_cluster),
+        cols = rows[hdr]
+        for r in rows[hdr + 1:]:
+            if len(r) != len(cols):
+                continue
+            rec = dict(zip(cols, r))
+            name = rec["Kernel Name"]
+            if not rec["Metric Name"].startswith("dram__bytes") or not any(k in name for k in kinds):
+                continue
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}[rec["Metric Unit"]]
+            v = float(rec["Metric Value"].replace(",", "")) * scale
+            key = name.split("(")[0].replace("void ", "")
+            per_kernel[key] = per_kernel.get(key, 0.0) + v
+            launches.setdefault(key, set()).add((path, rec["ID"]))
+    n, d, C = int(run["n"]), int(run["d"]), int(run["clusters"])
+    P = int(run["tune"]["slots"])
+    waves = (C + P - 1) // P
+    kernel_bytes = sum(per_kernel.values())
+    memsets = waves * memset_bytes_per_wave(n, P)
+    alg = ARC_BYTES * int(run["A"]) + VERTEX_BYTES * int(run["V"]) + C * n * (1 + 8 * d)
+    return {"traversal": {"dram_bytes_per_alg_byte": (kernel_bytes + memsets) / alg,
+                          "kernel_dram_bytes": int(kernel_bytes), "memset_bytes": int(memsets),
+                          "alg_bytes": int(alg), "clusters": C, "slots": P,
                           "per_kernel_bytes": {k: int(v) for k, v in sorted(per_kernel.items())},
+                          "launches_captured": {k: len(v) for k, v in sorted(launches.items())},
                           "source_hash": kernel_source_hash(), "measured_on": note}}
 
 
 def main():
     args = parse()
     if args.record_traffic:
-        return record_traffic(args.record_traffic, args.traffic_clusters,
-                              f"R-MAT scale {args.scale}, {args.traffic_clusters} star clusters, host-driven "
-                              f"rounds; scaled to the 256-cluster launch by cluster count")
+        return record_traffic(args.record_traffic, args.traffic_run,
+                              f"R-MAT scale {args.scale}, one host-driven runcli call; per-wave memsets counted "
+                              "from their sizes; scaled to a launch by its algorithmic bytes")
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)

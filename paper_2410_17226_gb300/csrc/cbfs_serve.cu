@@ -40,6 +40,8 @@ struct Request {
     const int32_t* pairs;  // caller's host memory, [q][2]
     uint16_t* out;         // caller's host memory, [q]
     int64_t q = 0;
+    bool pinned_pairs = false;  // page-locked: copied by DMA straight into the batch
+    bool pinned_out = false;    // page-locked: answers copied by DMA straight out of the batch
     int64_t packed = 0;     // pairs handed to batches so far
     int64_t remaining = 0;  // pairs not yet answered
     int status = CBFS_OK;
@@ -107,10 +109,10 @@ void run_waiter(cbfs_server_s* S, Slot* sl) {
         const Clock::time_point now = Clock::now();
         std::vector<Request*> finished;
         for (const Part& p : sl->parts) {
-            if (st == CBFS_OK)
-                std::memcpy(p.req->out + p.req_off, sl->h_out + p.batch_off, sizeof(uint16_t) * (size_t)p.count);
-            else
+            if (st != CBFS_OK)
                 p.req->status = st;
+            else if (!p.req->pinned_out)  // page-locked outputs were written by DMA
+                std::memcpy(p.req->out + p.req_off, sl->h_out + p.batch_off, sizeof(uint16_t) * (size_t)p.count);
         }
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -165,16 +167,43 @@ void run_dispatcher(cbfs_server_s* S) {
             S->used += sl->bytes;
         }
         // staging and launch outside the lock (the parts' requests stay alive:
-        // a request is released only after it is done)
-        for (const Part& p : sl->parts)
-            std::memcpy(sl->h_pairs + 2 * p.batch_off, p.req->pairs + 2 * p.req_off, sizeof(int32_t) * 2 * (size_t)p.count);
+        // a request is released only after it is done).  Page-locked request
+        // buffers are copied by DMA directly; the others through the slot's
+        // page-locked staging, one host memcpy each way.
         int st = CBFS_OK;
-        if (cudaMemcpyAsync(sl->d_pairs, sl->h_pairs, sizeof(int32_t) * 2 * (size_t)sl->count, cudaMemcpyHostToDevice,
+        int64_t staged_lo = -1, staged_hi = -1;  // batch range of the staged parts
+        for (const Part& p : sl->parts) {
+            if (p.req->pinned_pairs) {
+                if (cudaMemcpyAsync(sl->d_pairs + 2 * p.batch_off, p.req->pairs + 2 * p.req_off,
+                                    sizeof(int32_t) * 2 * (size_t)p.count, cudaMemcpyHostToDevice, sl->stream) != cudaSuccess)
+                    st = CBFS_E_CUDA;
+                continue;
+            }
+            std::memcpy(sl->h_pairs + 2 * p.batch_off, p.req->pairs + 2 * p.req_off, sizeof(int32_t) * 2 * (size_t)p.count);
+            if (staged_lo < 0) staged_lo = p.batch_off;
+            staged_hi = p.batch_off + p.count;
+        }
+        if (st == CBFS_OK && staged_lo >= 0 &&
+            cudaMemcpyAsync(sl->d_pairs + 2 * staged_lo, sl->h_pairs + 2 * staged_lo,
+                            sizeof(int32_t) * 2 * (size_t)(staged_hi - staged_lo), cudaMemcpyHostToDevice,
                             sl->stream) != cudaSuccess)
             st = CBFS_E_CUDA;
         if (st == CBFS_OK) st = cbfs_query_distance(S->labels, sl->d_pairs, sl->count, sl->d_out, sl->stream);
-        if (st == CBFS_OK && cudaMemcpyAsync(sl->h_out, sl->d_out, sizeof(uint16_t) * (size_t)sl->count,
-                                             cudaMemcpyDeviceToHost, sl->stream) != cudaSuccess)
+        int64_t out_lo = -1, out_hi = -1;
+        for (const Part& p : sl->parts) {
+            if (st != CBFS_OK) break;
+            if (p.req->pinned_out) {
+                if (cudaMemcpyAsync(p.req->out + p.req_off, sl->d_out + p.batch_off, sizeof(uint16_t) * (size_t)p.count,
+                                    cudaMemcpyDeviceToHost, sl->stream) != cudaSuccess)
+                    st = CBFS_E_CUDA;
+                continue;
+            }
+            if (out_lo < 0) out_lo = p.batch_off;
+            out_hi = p.batch_off + p.count;
+        }
+        if (st == CBFS_OK && out_lo >= 0 &&
+            cudaMemcpyAsync(sl->h_out + out_lo, sl->d_out + out_lo, sizeof(uint16_t) * (size_t)(out_hi - out_lo),
+                            cudaMemcpyDeviceToHost, sl->stream) != cudaSuccess)
             st = CBFS_E_CUDA;
         if (st == CBFS_OK && cudaEventRecord(sl->ev, sl->stream) != cudaSuccess) st = CBFS_E_CUDA;
         if (st != CBFS_OK) cudaGetLastError();
@@ -190,6 +219,16 @@ void run_dispatcher(cbfs_server_s* S) {
         S->dispatcher_done = true;
     }
     S->cv_slot.notify_all();
+}
+
+// True for page-locked host memory (cudaHostAlloc / cudaHostRegister).
+bool is_page_locked(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
 }
 
 void free_slot(Slot* sl) {
@@ -267,6 +306,10 @@ int cbfs_server_submit(cbfs_server_t S, const int32_t* host_pairs, int64_t q, ui
     r->pairs = host_pairs;
     r->out = host_out;
     r->q = q;
+    if (q > 0) {
+        r->pinned_pairs = is_page_locked(host_pairs);
+        r->pinned_out = is_page_locked(host_out);
+    }
     r->remaining = q;
     r->t_arrival = Clock::now();
     {

@@ -103,10 +103,19 @@ class QueryServer:
         self.max_batch, self.budget = int(c[3]), int(c[4])
 
     # ----------------------------------------------------------------- API
-    def submit(self, pairs) -> Ticket:
-        """Queue a request (int32 [q, 2] vertex pairs); ``result()`` yields uint16 [q]."""
+    def submit(self, pairs, out: np.ndarray | None = None) -> Ticket:
+        """Queue a request (int32 [q, 2] vertex pairs); ``result()`` yields
+        uint16 [q], written into ``out`` when given (a contiguous uint16 array
+        of q entries).  Page-locked buffers (``cbfs.pinned_empty``) are copied
+        by DMA with no host copy in the server; both must stay untouched
+        until ``result()`` returns."""
+        if isinstance(pairs, torch.Tensor):
+            pairs = pairs.numpy()
         p = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
-        out = np.empty(p.shape[0], dtype=np.uint16)
+        if out is None:
+            out = np.empty(p.shape[0], dtype=np.uint16)
+        elif out.dtype != np.uint16 or out.shape != (p.shape[0],) or not out.flags.c_contiguous:
+            raise ValueError("out must be a contiguous uint16 array with one entry per pair")
         tid = ctypes.c_uint64()
         cbfs._check(cbfs.lib().cbfs_server_submit(self._h, p.ctypes.data if p.size else None, int(p.shape[0]),
                                                   out.ctypes.data if p.size else None, ctypes.byref(tid)),
@@ -161,18 +170,51 @@ class QueryServer:
                     "cbfs_server_stats")
         lat = lat[:max(min(n.value, lat.size), 1)]
         return {"requests": int(c[0]), "batches": int(c[1]), "pairs": int(c[2]),
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "p50_ms": float(np.percentile(lat, 50)), "p90_ms": float(np.percentile(lat, 90)),
+                "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
                 "mean_ms": float(lat.mean()), "max_batch": int(c[3]), "budget_bytes": int(c[4])}
 
 
-def poisson_load(server: QueryServer, n: int, rate_rps: float, duration_s: float, max_pairs: int, seed: int):
+class RequestPool:
+    """Requests of a load generator: slices of one pool of uniform random
+    pairs, and answer buffers from a ring (the ticket that last used a ring
+    entry is waited for before the entry is reused).  ``pinned`` puts both in
+    page-locked memory, which the server copies by DMA."""
+
+    def __init__(self, n: int, max_pairs: int, seed: int, pinned: bool = False, ring: int = 512):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        pairs = rng.integers(0, n, size=(4 * max_pairs, 2), dtype=np.int64).astype(np.int32)
+        if pinned:
+            self.pairs = cbfs.pinned_empty(pairs.shape, torch.int32).numpy()
+            self.pairs[:] = pairs
+            self.outs = cbfs.pinned_empty((ring, max_pairs), torch.int16).numpy().view(np.uint16)
+        else:
+            self.pairs = pairs
+            self.outs = np.empty((ring, max_pairs), np.uint16)
+        self.users = [None] * ring
+        self.next = 0
+
+    def submit(self, server: QueryServer, start: int, q: int) -> Ticket:
+        i = self.next
+        self.next = (i + 1) % len(self.users)
+        if self.users[i] is not None:
+            self.users[i].result()
+        t = server.submit(self.pairs[start:start + q], out=self.outs[i, :q])
+        self.users[i] = t
+        return t
+
+
+def poisson_load(server: QueryServer, n: int, rate_rps: float, duration_s: float, max_pairs: int, seed: int,
+                 pinned: bool = False):
     """Offers requests with exponential inter-arrival times (rate_rps per
     second) and sizes uniform in 1..max_pairs for duration_s seconds; each
-    request is a slice of a pregenerated pool of uniform random pairs, so the
-    client itself is not the bottleneck.  Returns (tickets, pairs offered,
-    elapsed seconds)."""
+    request is a slice of a pregenerated pool of uniform random pairs
+    (``RequestPool``; page-locked with ``pinned``), so the client itself is
+    not the bottleneck.  Returns (tickets, pairs offered, elapsed seconds).
+    With ``pinned`` a ticket's answers stay valid only until its answer
+    buffer is reused, 512 requests later."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    pool = rng.integers(0, n, size=(4 * max_pairs, 2), dtype=np.int64).astype(np.int32)
+    pool = RequestPool(n, max_pairs, seed=int(rng.integers(1 << 62)), pinned=pinned)
     gaps = rng.exponential(1.0 / rate_rps, size=1 << 16)
     sizes = rng.integers(1, max_pairs + 1, size=1 << 16)
     starts = rng.integers(0, 3 * max_pairs + 1, size=1 << 16)
@@ -188,7 +230,7 @@ def poisson_load(server: QueryServer, n: int, rate_rps: float, duration_s: float
         if t_next > now:
             time.sleep(t_next - now)
         q, s0 = int(sizes[i % sizes.size]), int(starts[i % starts.size])
-        futs.append(server.submit(pool[s0:s0 + q]))
+        futs.append(pool.submit(server, s0, q))
         offered += q
         i += 1
     for f in futs:

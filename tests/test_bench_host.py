@@ -17,22 +17,32 @@ def _write_csv(path, rows):
 
 
 def test_traffic_from_csv(tmp_path):
-    p = tmp_path / "t.csv"
-    _write_csv(p, [
+    """Two captures (one kernel each) summed per kernel, units scaled, memsets
+    counted per wave, divided by the captured call's algorithmic bytes."""
+    p1, p2 = tmp_path / "a.csv", tmp_path / "b.csv"
+    _write_csv(p1, [
         ["0", "void cbfs::k_phase_a<4>(cbfs::Wave, int)", "dram__bytes_read.sum", "Mbyte", "100"],
         ["0", "void cbfs::k_phase_a<4>(cbfs::Wave, int)", "dram__bytes_write.sum", "Mbyte", "50"],
-        ["1", "void cbfs::k_phase_b<4>(cbfs::Wave, int)", "dram__bytes_read.sum", "Gbyte", "1.5"],
-        ["1", "void cbfs::k_phase_b<4>(cbfs::Wave, int)", "dram__bytes_write.sum", "byte", "1,000"],
         ["2", "k_validate(long, const long *, ...)", "dram__bytes_read.sum", "Gbyte", "9"],  # not traversal
         ["3", "void cbfs::k_emit<4>(cbfs::Wave, const int *)", "gpu__time_duration.sum", "us", "5"],  # not bytes
     ])
-    out = bench.traffic_from_csv(str(p), 2, "test")["traversal"]
-    total = 100e6 + 50e6 + 1.5e9 + 1000
-    assert out["per_cluster_bytes"] == int(total / 2)
-    assert out["dram_bytes_per_launch"] == int(total / 2 * 256)
+    _write_csv(p2, [
+        ["0", "void cbfs::k_phase_b<4>(cbfs::Wave, int)", "dram__bytes_read.sum", "Gbyte", "1.5"],
+        ["0", "void cbfs::k_phase_b<4>(cbfs::Wave, int)", "dram__bytes_write.sum", "byte", "1,000"],
+        ["1", "void cbfs::k_phase_b<4>(cbfs::Wave, int)", "dram__bytes_read.sum", "Mbyte", "2"],
+    ])
+    run = {"n": 1000, "d": 2, "clusters": 4, "A": 10_000_000, "V": 100_000, "tune": {"slots": 4}}
+    out = bench.traffic_from_csv([str(p1), str(p2)], run, "test")["traversal"]
+    kernels = 100e6 + 50e6 + 1.5e9 + 1000 + 2e6
+    memsets = bench.memset_bytes_per_wave(1000, 4)
+    alg = 13 * 10_000_000 + 41 * 100_000 + 4 * 1000 * 17
+    assert out["kernel_dram_bytes"] == int(kernels) and out["memset_bytes"] == memsets
+    assert abs(out["dram_bytes_per_alg_byte"] - (kernels + memsets) / alg) < 1e-12
     assert out["per_kernel_bytes"]["cbfs::k_phase_a<4>"] == int(150e6)
+    assert out["launches_captured"]["cbfs::k_phase_b<4>"] == 2
     assert "k_validate" not in " ".join(out["per_kernel_bytes"])
     assert out["source_hash"] == bench.kernel_source_hash() and len(out["source_hash"]) == 16
+    assert memsets == (16 * 4 + 4 + 4) * 1000 + 2 * 4 * 33 + 288 * 56
 
 
 def test_summary_of_a_line_keeps_every_workload():
