@@ -450,19 +450,24 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
     source-edge GTEPS and the algorithmic-byte rate beside the HBM peak."""
     import torch
 
+    from paper_2410_17226_gb300 import tune
+
     off, adj = I.road_grid(side, seed=I.MASTER_SEED + 2)
     clusters, ds = I.ball_clusters(off, adj, count, 64, seed=seed)
     d = max(ds)
     deg = np.diff(off)
     with cbfs.Graph(off, adj) as g:
         n = g.n
+        # this graph's own switch factor, clusters per wave and degree classes
+        tn = tune.autotune(g, clusters, d, sample=per_launch, key_extra=f"grid-{side}-{tune.signature(off)}")
+        tset = {k: tn[k] for k in ("pull_alpha", "slots", "small_deg", "mid_deg")}
         dist = torch.empty((per_launch, n), dtype=torch.uint8, device="cuda")
         masks = torch.empty((per_launch, d, n), dtype=torch.int64, device="cuda")
         total_ms, A, V, src_edges, rounds = 0.0, 0, 0, 0, 0
         for b in range(0, count, per_launch):
             part = clusters[b:b + per_launch]
             k = len(part)
-            run = lambda: g.run_batched(part, d, dist[:k], masks[:k])  # noqa: E731
+            run = lambda: g.run_batched(part, d, dist[:k], masks[:k], tune=tset)  # noqa: E731
             total_ms += timed_ms(run, reps=2)
             st = g.output_stats(dist[:k], masks[:k], [len(S) for S in part], d)
             A += int(st[:, 1].sum())
@@ -476,7 +481,8 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
         torch.cuda.empty_cache()
     peak, _ = measured_peak_hbm()
     return {"graph": f"road grid {side}x{side}, 10% deleted, 1% shortcuts", "n": int(n), "nnz": int(adj.size),
-            "clusters": count, "d": d, "per_launch": per_launch, "ms_all_clusters": round(total_ms, 2),
+            "clusters": count, "d": d, "per_launch": per_launch, "tune": dict(tset, cached=tn.get("cached")),
+            "ms_all_clusters": round(total_ms, 2),
             "gteps": round(src_edges / (total_ms / 1e3) / 1e9, 2), "max_rounds": rounds,
             "arcs_per_s": round(A / (total_ms / 1e3), 1),
             "alg_gbs": round(alg / (total_ms / 1e3) / 1e9, 1), "alg_frac": round(alg / (total_ms / 1e3) / 1e9 / peak, 4)}
@@ -815,6 +821,52 @@ def run_cbfs(args, ws, rank, local):
                        "peak_gbs": peak, "frac": round(q_alg / (q_ms / 1e3) / 1e9 / peak, 4),
                        "note": "random rows of 4.4 KB (256 clusters x 17 B): the label store (18 GB) exceeds L2"}
 
+    # serving (continuous batching) over labels of 60 degree-ordered clusters of the same graph
+    serving = None
+    if args.serve_s > 0:
+        from paper_2410_17226_gb300.serve import QueryServer, RequestPool, poisson_load
+
+        lab_clusters, _ = I.degree_clusters(off, adj, 60)
+        ld, lm = g.run_batched(lab_clusters, d, tune=tset)
+        L60 = cbfs.Labels(n, len(lab_clusters), d)
+        L60.append(ld, lm, [len(S) for S in lab_clusters])
+        del ld, lm
+        torch.cuda.synchronize()
+        serve_batch = 4 * args.query_batch  # one launch may pack several requests
+        sopt = {"pause_gc": True, "switch_interval_s": 1e-4}
+        with QueryServer(L60, max_batch=serve_batch, slots=4, **sopt) as srv:
+            # saturation: the same request mix (sizes uniform in 1..65536) offered as fast as possible
+            rng = np.random.default_rng(rank_seed(rank) + 13)
+            pool = RequestPool(n, args.query_batch, seed=rank_seed(rank) + 13, pinned=True)
+            sizes = rng.integers(1, args.query_batch + 1, size=3000)
+            starts = rng.integers(0, 3 * args.query_batch + 1, size=3000)
+            for i in range(50):
+                pool.submit(srv, int(starts[i]), int(sizes[i]))
+            t0 = time.perf_counter()
+            futs = [pool.submit(srv, int(starts[i]), int(sizes[i])) for i in range(50, 3000)]
+            for f in futs:
+                f.result()
+            sat_qps = float(sizes[50:].sum()) / (time.perf_counter() - t0)
+        loads = {}
+        mean_req = (args.query_batch + 1) / 2.0
+        for load in (0.5, 0.8):
+            with QueryServer(L60, max_batch=serve_batch, slots=4, **sopt) as srv:
+                futs, offered, elapsed = poisson_load(srv, n, rate_rps=load * sat_qps / mean_req,
+                                                      duration_s=args.serve_s, max_pairs=args.query_batch,
+                                                      seed=rank_seed(rank) + int(load * 100), pinned=True)
+                st_ = srv.stats()
+            loads[f"{load}x"] = {"p50_ms": round(st_["p50_ms"], 4), "p90_ms": round(st_["p90_ms"], 4),
+                                 "p99_ms": round(st_["p99_ms"], 4), "max_ms": round(st_["max_ms"], 4),
+                                 "qps": round(offered / elapsed, 1), "requests": st_["requests"],
+                                 "batches": st_["batches"]}
+        serving = {"labels": "60 degree-ordered clusters (Section 4.2 selection), d=2, 1020 B/vertex",
+                   "server_options": sopt,
+                   "arrivals": "Poisson, request sizes uniform in 1..65536 pairs, page-locked request and "
+                               "answer buffers (copied by DMA)",
+                   "saturation_qps": round(sat_qps, 1), "max_batch_pairs": serve_batch,
+                   "offered": loads}
+        del L60
+
     # single-source BFS comparison and the d sweep (the same resident graph)
     nxt = None
     if args.next_rows and rank == 0:
@@ -828,50 +880,6 @@ def run_cbfs(args, ws, rank, local):
         nxt["d_sweep"] = sweep
         nxt["ll_quality"] = ll_quality(cbfs, g, off, adj, seed=rank_seed(rank) + 24)
         nxt["road_grid"] = road_grid_throughput(cbfs, seed=I.MASTER_SEED + 3)
-
-    # serving (continuous batching) over labels of 60 degree-ordered clusters of the same graph
-    serving = None
-    if args.serve_s > 0:
-        from paper_2410_17226_gb300.serve import QueryServer, poisson_load
-
-        lab_clusters, _ = I.degree_clusters(off, adj, 60)
-        ld, lm = g.run_batched(lab_clusters, d, tune=tset)
-        L60 = cbfs.Labels(n, len(lab_clusters), d)
-        L60.append(ld, lm, [len(S) for S in lab_clusters])
-        del ld, lm
-        torch.cuda.synchronize()
-        serve_batch = 4 * args.query_batch  # one launch may pack several requests
-        sopt = {"pause_gc": True, "switch_interval_s": 1e-4}
-        with QueryServer(L60, max_batch=serve_batch, slots=4, **sopt) as srv:
-            # saturation: the same request mix (sizes uniform in 1..65536) offered as fast as possible
-            rng = np.random.default_rng(rank_seed(rank) + 13)
-            pool = rng.integers(0, n, size=(4 * args.query_batch, 2)).astype(np.int32)
-            sizes = rng.integers(1, args.query_batch + 1, size=3000)
-            starts = rng.integers(0, 3 * args.query_batch + 1, size=3000)
-            for i in range(50):
-                srv.submit(pool[starts[i]:starts[i] + sizes[i]])
-            t0 = time.perf_counter()
-            futs = [srv.submit(pool[starts[i]:starts[i] + sizes[i]]) for i in range(50, 3000)]
-            for f in futs:
-                f.result()
-            sat_qps = float(sizes[50:].sum()) / (time.perf_counter() - t0)
-        loads = {}
-        mean_req = (args.query_batch + 1) / 2.0
-        for load in (0.5, 0.8):
-            with QueryServer(L60, max_batch=serve_batch, slots=4, **sopt) as srv:
-                futs, offered, elapsed = poisson_load(srv, n, rate_rps=load * sat_qps / mean_req,
-                                                      duration_s=args.serve_s, max_pairs=args.query_batch,
-                                                      seed=rank_seed(rank) + int(load * 100))
-                st_ = srv.stats()
-            loads[f"{load}x"] = {"p50_ms": round(st_["p50_ms"], 4), "p99_ms": round(st_["p99_ms"], 4),
-                                 "qps": round(offered / elapsed, 1), "requests": st_["requests"],
-                                 "batches": st_["batches"]}
-        serving = {"labels": "60 degree-ordered clusters (Section 4.2 selection), d=2, 1020 B/vertex",
-                   "server_options": sopt,
-                   "arrivals": "Poisson, request sizes uniform in 1..65536 pairs",
-                   "saturation_qps": round(sat_qps, 1), "max_batch_pairs": serve_batch,
-                   "offered": loads}
-        del L60
 
     # End to end through the public API: the CSR from page-locked host memory
     # (H2D inside graph create), the batched traversal writing the label store

@@ -105,7 +105,12 @@ typedef struct cbfs_tune_s {
        n/32 vertices (lists rarely end early there).  0 or < 0 = use mid_deg
        in every round (the default: other limits were measured no faster). */
     int sparse_mid_deg;
-    int reserved[1];
+    /* how the clusters of a call with device outputs are grouped into waves:
+       0 = by size (sizes descending, ties in call order: the clusters of a
+       wave then finish in similar rounds and small ones pull and stop
+       early), 1 = in call order.  Host outputs and label stores always use
+       call order. */
+    int wave_order;
 } cbfs_tune_t;
 
 /* Work counters of one cluster's traversal (Theorem 1). */

@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             zero_words<P>(w.acc + (size_t)u * P);
             if (!any) continue;
             if (w.dist_r) {
-                // the wave's internal rows of u
+                // the wave's internal rows of u: P Delta bytes, then each slot's
+                // d subset words contiguous (slot s at mr[s*d .. s*d + d))
                 uint8_t* dr = w.dist_r + (size_t)u * P;
                 uint64_t* mr = w.masks_r + (size_t)u * w.d * P;
 #pragma unroll
@@ -449,12 +450,13 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                         else dr[s] = (uint8_t)round;
                         j = 0;
                         // first visit of slot s: its subset words start empty here
-                        // (the rows are not cleared per wave; k_emit ignores unreached slots)
-                        for (int jj = 1; jj < w.d; ++jj) mr[(size_t)jj * P + s] = 0ull;
+                        // (the rows are not cleared per wave; k_emit ignores unreached
+                        // slots); the slot's words are contiguous, so this writes whole sectors
+                        for (int jj = 1; jj < w.d; ++jj) mr[(size_t)s * w.d + jj] = 0ull;
                     } else {
                         j = round - (int)dd;
                     }
-                    if (j < w.d) mr[(size_t)j * P + s] = fw[r][s];
+                    if (j < w.d) mr[(size_t)s * w.d + j] = fw[r][s];
                     else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
                     my_active |= 1u << s;
                 }
@@ -798,16 +800,10 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
             if (dv != 0xFF) reached |= 1u << s;
         }
         for (int j = 0; j < d; ++j) {
-            uint64_t m[P];
-            if (reached) {
-                load_words<P>(mr + (size_t)j * P, m);
-            } else {
-#pragma unroll
-                for (int s = 0; s < P; ++s) m[s] = 0ull;
-            }
 #pragma unroll
             for (int s = 0; s < P; ++s)
-                if (s < w.nslots) ss[s].masks[(size_t)j * (size_t)w.n + v] = ((reached >> s) & 1u) ? m[s] : 0ull;
+                if (s < w.nslots)
+                    ss[s].masks[(size_t)j * (size_t)w.n + v] = ((reached >> s) & 1u) ? mr[(size_t)s * d + j] : 0ull;
         }
     }
 }
@@ -1470,10 +1466,16 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     // (measured: 0.02 vs 0.08 is 1.5x faster for k = 2..4, equal from k = 8).
     const bool alpha_given = tune && tune->pull_alpha != 0.f;
     const float alpha = alpha_given ? tune->pull_alpha : 0.08f;
+    // order[pos]: the cluster in wave pos / P, slot pos % P (set below)
+    std::vector<int> order((size_t)C);
+    for (int c = 0; c < C; ++c) order[c] = c;
     auto wave_alpha = [&](int wv) -> float {
         if (alpha_given) return alpha;
         int max_k = 0;
-        for (int c = wv * P; c < std::min(C, (wv + 1) * P); ++c) max_k = std::max(max_k, coff[c + 1] - coff[c]);
+        for (int pos = wv * P; pos < std::min(C, (wv + 1) * P); ++pos) {
+            const int c = order[pos];
+            max_k = std::max(max_k, coff[c + 1] - coff[c]);
+        }
         return max_k <= 4 ? 0.02f : 0.08f;
     };
     int dense_div = 16;
@@ -1529,6 +1531,16 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         while (G % CG) CG--;
     }
     const int LG = L ? (staged ? G : std::max(1, kLabelGroup / P)) : 0;  // waves per label write
+    // Wave composition.  With device outputs and no label store every slot
+    // writes through its own output pointers, so clusters may be traversed in
+    // any grouping: clusters of similar size share a wave (sizes descending,
+    // ties in call order).  A wave of small clusters then pulls early and its
+    // pulls stop early, instead of running as long as one large cluster in
+    // its midst.  Staged outputs and label rows are written per wave in call
+    // order, so those calls keep it.
+    if (!staged && !L && !(tune && tune->wave_order == 1))
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return coff[a + 1] - coff[a] > coff[b + 1] - coff[b]; });
     const int64_t stage_dist_bytes = (G * wave_dist + 255) / 256 * 256;
     if (staged) {
         rc = ensure_dev(&g->stage, &g->stage_cap, stage_dist_bytes + 8 * G * wave_masks);
@@ -1569,13 +1581,19 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     for (int wv = 0; wv < nwaves; ++wv) {
         wave_seed_off[wv] = ns;
         for (int s = 0; s < P; ++s) {
-            const int c = wv * P + s;
+            const int pos = wv * P + s;
             SlotDesc sd;
             memset(&sd, 0, sizeof(sd));
-            if (c < C) {
+            if (pos < C) {
+                const int c = order[pos];  // == pos when staged or with labels
                 const int k = coff[c + 1] - coff[c];
-                sd.dist = wave_dist_at(wv) + (size_t)s * (size_t)n;
-                sd.masks = d ? wave_masks_at(wv) + (size_t)s * (size_t)d * (size_t)n : nullptr;
+                if (staged) {
+                    sd.dist = wave_dist_at(wv) + (size_t)s * (size_t)n;
+                    sd.masks = d ? wave_masks_at(wv) + (size_t)s * (size_t)d * (size_t)n : nullptr;
+                } else {
+                    sd.dist = dist + (size_t)c * (size_t)n;
+                    sd.masks = d ? masks + (size_t)c * (size_t)d * (size_t)n : nullptr;
+                }
                 sd.all = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
                 sd.cluster = c;
                 for (int j = 0; j < k; ++j)

@@ -106,7 +106,7 @@ struct Wave {
     int64_t n_small, n_mid, n_big;
     const int32_t* perm;    // internal vertex -> caller's id for the outputs (nullptr: identity)
     uint8_t* dist_r;        // [n][P] Delta rows of the wave in internal order, emitted to the
-    uint64_t* masks_r;      // [n][d][P] caller's arrays after the wave; nullptr: the vertex
+    uint64_t* masks_r;      // [n][P][d] caller's arrays after the wave; nullptr: the vertex
                             // phase writes the caller's arrays directly (P = 1, no perm)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
     int* round_dev;         // graph mode: the current round lives here (nullptr: kernel argument)

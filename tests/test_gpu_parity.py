@@ -111,6 +111,25 @@ def test_batched_equals_single_and_oracle(cb):
         assert (cb.as_numpy_u64(single[c][1]) == om).all()
 
 
+def test_waves_grouped_by_size_or_in_call_order(cb):
+    """Clusters of mixed sizes: the default groups them into waves by size,
+    wave_order = 1 keeps the call order; both, host-driven and replayed,
+    equal the oracle cluster by cluster (outputs stay at the call's
+    positions whatever wave a cluster ran in)."""
+    off, adj = I.rmat(12, seed=23)
+    g = cb.Graph(off, adj)
+    stars, d = I.star_clusters(off, adj, 11, seed=8, size="max", min_deg=63)
+    sizes = [1, 64, 2, 33, 5, 64, 1, 7, 3, 40, 2]
+    clusters = [S[:k] for S, k in zip(stars, sizes)]
+    want = [O.cbfs_alg1(off, adj, S, d) for S in clusters]
+    for tune in ({"slots": 4}, {"slots": 4, "wave_order": 1}, {"slots": 8, "host_loop": 1},
+                 {"slots": 2, "wave_order": 1, "host_loop": 1}):
+        for rep in range(2):
+            bd, bm = g.run_batched(clusters, d, tune=tune)
+            for c, (od, om) in enumerate(want):
+                assert (bd[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(bm[c]) == om).all(), (tune, rep, c)
+
+
 def test_graph_replay_with_new_sources_each_call(cb):
     """A cached graph replays a call shape; the sources of every call are
     uploaded before the replay, so different clusters of the same shape give

@@ -107,3 +107,40 @@ def test_server_restores_interpreter_settings(setup):
         assert not gc.isenabled() and abs(sys.getswitchinterval() - 2e-4) < 1e-9
         srv.submit(np.zeros((3, 2), np.int32)).result()
     assert (gc.isenabled(), sys.getswitchinterval()) == before
+
+
+def test_page_locked_requests_and_answer_buffers(setup):
+    """Requests and answer buffers in page-locked memory are copied by DMA
+    (no host copy in the server); pageable and page-locked requests mixed in
+    one server give the oracle's answers."""
+    cbfs, g, L, dist, masks, ks = setup
+    from paper_2410_17226_gb300.serve import QueryServer, RequestPool
+
+    reqs = make_requests(g.n, 40, seed=9, max_pairs=5000)
+    pinned = []
+    for r in reqs[::2]:
+        p = cbfs.pinned_empty(r.shape, torch.int32).numpy()
+        p[:] = r
+        pinned.append(p)
+    outs = [cbfs.pinned_empty(r.shape[0], torch.int16).numpy().view(np.uint16) for r in reqs[::2]]
+    with QueryServer(L, max_batch=4096, slots=3) as srv:
+        futs = []
+        for i, r in enumerate(reqs):
+            if i % 2 == 0:
+                futs.append(srv.submit(pinned[i // 2], out=outs[i // 2]))
+            else:
+                futs.append(srv.submit(r))
+        got = [f.result() for f in futs]
+    for i, (r, a) in enumerate(zip(reqs, got)):
+        assert (a == O.query(dist, masks, ks, r)).all(), i
+        if i % 2 == 0:
+            assert a is outs[i // 2]
+    # the load generator's page-locked pool: answers equal the oracle's
+    pool = RequestPool(g.n, 3000, seed=4, pinned=True, ring=8)
+    with QueryServer(L, max_batch=2048, slots=2) as srv:
+        t = pool.submit(srv, 100, 2500)
+        a = t.result().copy()
+    assert (a == O.query(dist, masks, ks, pool.pairs[100:2600])).all()
+    with QueryServer(L, max_batch=16, slots=1) as srv:
+        with pytest.raises(ValueError):
+            srv.submit(reqs[1], out=np.empty(3, np.uint16))
