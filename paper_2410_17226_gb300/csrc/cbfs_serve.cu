@@ -170,24 +170,29 @@ void run_dispatcher(cbfs_server_s* S) {
         // a request is released only after it is done).  Page-locked request
         // buffers are copied by DMA directly; the others through the slot's
         // page-locked staging, one host memcpy each way.
+        // The staged parts go in one copy of the batch range they span, which
+        // may include page-locked parts; those are copied after it on the same
+        // stream, so their own pairs overwrite whatever the range carried.
         int st = CBFS_OK;
         int64_t staged_lo = -1, staged_hi = -1;  // batch range of the staged parts
         for (const Part& p : sl->parts) {
-            if (p.req->pinned_pairs) {
-                if (cudaMemcpyAsync(sl->d_pairs + 2 * p.batch_off, p.req->pairs + 2 * p.req_off,
-                                    sizeof(int32_t) * 2 * (size_t)p.count, cudaMemcpyHostToDevice, sl->stream) != cudaSuccess)
-                    st = CBFS_E_CUDA;
-                continue;
-            }
+            if (p.req->pinned_pairs) continue;
             std::memcpy(sl->h_pairs + 2 * p.batch_off, p.req->pairs + 2 * p.req_off, sizeof(int32_t) * 2 * (size_t)p.count);
             if (staged_lo < 0) staged_lo = p.batch_off;
             staged_hi = p.batch_off + p.count;
         }
-        if (st == CBFS_OK && staged_lo >= 0 &&
+        if (staged_lo >= 0 &&
             cudaMemcpyAsync(sl->d_pairs + 2 * staged_lo, sl->h_pairs + 2 * staged_lo,
                             sizeof(int32_t) * 2 * (size_t)(staged_hi - staged_lo), cudaMemcpyHostToDevice,
                             sl->stream) != cudaSuccess)
             st = CBFS_E_CUDA;
+        for (const Part& p : sl->parts) {
+            if (st != CBFS_OK) break;
+            if (p.req->pinned_pairs &&
+                cudaMemcpyAsync(sl->d_pairs + 2 * p.batch_off, p.req->pairs + 2 * p.req_off,
+                                sizeof(int32_t) * 2 * (size_t)p.count, cudaMemcpyHostToDevice, sl->stream) != cudaSuccess)
+                st = CBFS_E_CUDA;
+        }
         if (st == CBFS_OK) st = cbfs_query_distance(S->labels, sl->d_pairs, sl->count, sl->d_out, sl->stream);
         int64_t out_lo = -1, out_hi = -1;
         for (const Part& p : sl->parts) {
