@@ -799,11 +799,12 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
             ss[s].dist[v] = dv;
             if (dv != 0xFF) reached |= 1u << s;
         }
-        for (int j = 0; j < d; ++j) {
+        // slot by slot: a slot's d words are contiguous in the row
 #pragma unroll
-            for (int s = 0; s < P; ++s)
-                if (s < w.nslots)
-                    ss[s].masks[(size_t)j * (size_t)w.n + v] = ((reached >> s) & 1u) ? mr[(size_t)s * d + j] : 0ull;
+        for (int s = 0; s < P; ++s) {
+            if (s >= w.nslots) continue;
+            const bool rs = (reached >> s) & 1u;
+            for (int j = 0; j < d; ++j) ss[s].masks[(size_t)j * (size_t)w.n + v] = rs ? mr[(size_t)s * d + j] : 0ull;
         }
     }
 }

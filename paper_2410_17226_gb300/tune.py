@@ -24,8 +24,8 @@ import torch
 from . import cbfs
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
-ALPHAS = (0.005, 0.01, 0.02, 0.04, 0.08, 0.2, 0.4, -1.0)  # -1: push only
-SLOTS = (2, 4, 8)
+ALPHAS = (0.005, 0.01, 0.02, 0.04, 0.08, 0.2, 0.4, 0.6, -1.0)  # -1: push only
+SLOTS = (1, 2, 4, 8)
 SMALL_DEGS = (8, 16, 32)          # one thread per vertex up to this degree
 MID_DEGS = (1024, 2048, 4096, 16384, 65536)  # one warp per vertex up to this degree, CTA pieces above
 
