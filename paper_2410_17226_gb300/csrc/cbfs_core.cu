@@ -440,23 +440,29 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                 // d subset words contiguous (slot s at mr[s*d .. s*d + d))
                 uint8_t* dr = w.dist_r + (size_t)u * P;
                 uint64_t* mr = w.masks_r + (size_t)u * w.d * P;
+                uint16_t* wr = w.wmask_r + (size_t)u * P;
 #pragma unroll
                 for (int s = 0; s < P; ++s) {
                     if (!fw[r][s]) continue;
                     const uint8_t dd = dr[s];
                     int j;
+                    uint32_t wm;
                     if (dd == 0xFF) {
                         if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
                         else dr[s] = (uint8_t)round;
                         j = 0;
-                        // first visit of slot s: its subset words start empty here
-                        // (the rows are not cleared per wave; k_emit ignores unreached
-                        // slots); the slot's words are contiguous, so this writes whole sectors
-                        for (int jj = 1; jj < w.d; ++jj) mr[(size_t)s * w.d + jj] = 0ull;
+                        // first visit of slot s: the rows are not cleared per wave, so
+                        // the written-word mask starts here (k_emit outputs 0 for a
+                        // word whose bit is clear, and ignores unreached slots)
+                        wm = 0;
                     } else {
                         j = round - (int)dd;
+                        wm = wr[s];
                     }
-                    if (j < w.d) mr[(size_t)s * w.d + j] = fw[r][s];
+                    if (j < w.d) {
+                        mr[(size_t)s * w.d + j] = fw[r][s];
+                        wr[s] = (uint16_t)(wm | (1u << j));
+                    }
                     else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
                     my_active |= 1u << s;
                 }
@@ -790,6 +796,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
         const int64_t r = iperm ? iperm[v] : v;
         const uint8_t* dr = w.dist_r + (size_t)r * P;
         const uint64_t* mr = w.masks_r + (size_t)r * d * P;
+        const uint16_t* wr = w.wmask_r + (size_t)r * P;
         // a slot that never reached v has stale subset words in the row: write zeros
         unsigned int reached = 0;
 #pragma unroll
@@ -799,12 +806,14 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
             ss[s].dist[v] = dv;
             if (dv != 0xFF) reached |= 1u << s;
         }
-        // slot by slot: a slot's d words are contiguous in the row
+        // slot by slot: a slot's d words are contiguous in the row; a word the
+        // vertex phase did not write this wave (empty subset) is 0
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             if (s >= w.nslots) continue;
-            const bool rs = (reached >> s) & 1u;
-            for (int j = 0; j < d; ++j) ss[s].masks[(size_t)j * (size_t)w.n + v] = rs ? mr[(size_t)s * d + j] : 0ull;
+            const uint32_t wm = ((reached >> s) & 1u) && d ? wr[s] : 0u;
+            for (int j = 0; j < d; ++j)
+                ss[s].masks[(size_t)j * (size_t)w.n + v] = ((wm >> j) & 1u) ? mr[(size_t)s * d + j] : 0ull;
         }
     }
 }
@@ -957,6 +966,7 @@ struct cbfs_graph_s {
     int32_t* perm = nullptr;   // rank -> caller's id
     int32_t* iperm_d = nullptr;  // caller's id -> rank (device, for the output emit)
     uint8_t* dist_r = nullptr;   // internal output rows of a wave
+    uint16_t* wmask_r = nullptr; // per vertex and slot: which subset words the wave wrote
     uint64_t* masks_r = nullptr;
     int64_t masks_r_cap = 0;
     uint64_t* pull_pieces = nullptr;  // (rank << 32 | piece) of every vertex of degree > kPullMid
@@ -1085,6 +1095,7 @@ void free_scratch(cbfs_graph_s* g) {
     dev_free(g->q1);
     dev_free(g->fb);
     dev_free(g->dist_r);
+    dev_free(g->wmask_r);
     dev_free(g->t_pre);
     dev_free(g->t_ost);
     dev_free(g->t_fw);
@@ -1109,6 +1120,7 @@ int ensure_scratch(cbfs_graph_s* g, int P) {
     if (!rc) rc = dev_alloc(&g->q1, z.queue);
     if (!rc) rc = dev_alloc(&g->fb, 2 * z.bitmap);
     if (!rc) rc = dev_alloc(&g->dist_r, z.state);
+    if (!rc) rc = dev_alloc(&g->wmask_r, z.state);
     if (!rc) rc = dev_alloc(&g->t_pre, z.list);
     if (!rc) rc = dev_alloc(&g->t_ost, z.list);
     if (!rc) rc = dev_alloc(&g->t_fw, z.list * P);
@@ -1655,6 +1667,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.status = g->status;
     w.alpha = alpha;
     w.dist_r = g->dist_r;
+    w.wmask_r = g->wmask_r;
     w.masks_r = g->masks_r;
     w.dense_div = dense_div;
 
