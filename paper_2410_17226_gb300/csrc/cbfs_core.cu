@@ -175,12 +175,13 @@ struct Gath {
     static constexpr int G = 4;
 };
 
-// ORs into acc the vis blocks of the frontier neighbours among up to G arcs
-// adj[e], adj[e + step], ... below o1 (fb == nullptr: every neighbour); all
-// gathers are issued before any is used.
+// ORs into acc the src blocks (the sources new at each frontier neighbour)
+// of the frontier neighbours among up to G arcs adj[e], adj[e + step], ...
+// below o1 (fb == nullptr: every neighbour); all gathers are issued before
+// any is used.
 template <int P>
-__device__ __forceinline__ void gather(const Wave& w, const uint32_t* fb, const int32_t* adj, int64_t e, int64_t step,
-                                       int64_t o1, uint64_t (&acc)[P]) {
+__device__ __forceinline__ void gather(const uint64_t* src, const uint32_t* fb, const int32_t* adj, int64_t e,
+                                       int64_t step, int64_t o1, uint64_t (&acc)[P]) {
     constexpr int G = Gath<P>::G;
     int32_t u[G];
 #pragma unroll
@@ -192,7 +193,7 @@ __device__ __forceinline__ void gather(const Wave& w, const uint32_t* fb, const 
     uint64_t x[G][P];
 #pragma unroll
     for (int k = 0; k < G; ++k) {
-        if (u[k] >= 0) load_words<P>(w.vis + (size_t)u[k] * P, x[k]);
+        if (u[k] >= 0) load_words<P>(src + (size_t)u[k] * P, x[k]);
         else {
 #pragma unroll
             for (int s = 0; s < P; ++s) x[k][s] = 0;
@@ -281,24 +282,93 @@ __device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], cons
     return um;
 }
 
-// Pull result of v: keep the new part as acc[v].  A pull round writes no
-// queue (the next vertex phase scans densely); it only counts the new
-// frontier and its arcs for the next direction decision.
+// Records the sources fw new at u in round `round` in u's rows (Algorithm 1's
+// S_u[round - Delta_u] = Snew, Delta_u = round on the first visit of a slot):
+// the wave's internal rows (dist_r path) or the caller's arrays directly (one
+// slot in the caller's ids, ss[0]).  Returns the slots with new sources.
+template <int P>
+__device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, const uint64_t (&fw)[P], int round,
+                                                    const SlotDesc* ss) {
+    unsigned int act = 0;
+    if (w.dist_r) {
+        // the wave's internal rows of u: P Delta bytes, then each slot's d
+        // subset words contiguous (slot s at mr[s*d .. s*d + d))
+        uint8_t* dr = w.dist_r + (size_t)u * P;
+        uint64_t* mr = w.masks_r + (size_t)u * w.d * P;
+        uint16_t* wr = w.wmask_r + (size_t)u * P;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            if (!fw[s]) continue;
+            const uint8_t dd = dr[s];
+            int j;
+            uint32_t wm;
+            if (dd == 0xFF) {
+                if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
+                else dr[s] = (uint8_t)round;
+                j = 0;
+                // first visit of slot s: the rows are not cleared per wave, so
+                // the written-word mask starts here (k_emit outputs 0 for a
+                // word whose bit is clear, and ignores unreached slots)
+                wm = 0;
+            } else {
+                j = round - (int)dd;
+                wm = wr[s];
+            }
+            if (j < w.d) {
+                mr[(size_t)s * w.d + j] = fw[s];
+                wr[s] = (uint16_t)(wm | (1u << j));
+            } else if (j > w.d) {
+                set_status(w.status, CBFS_E_DIAMETER);
+            }
+            act |= 1u << s;
+        }
+    } else {
+        // direct: one cluster, caller's ids, caller's arrays
+        const SlotDesc& S = ss[0];
+        const uint8_t dd = S.dist[u];
+        int j;
+        if (dd == 0xFF) {
+            if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
+            else S.dist[u] = (uint8_t)round;
+            j = 0;
+        } else {
+            j = round - (int)dd;
+        }
+        if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = fw[0];
+        else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
+        act = 1u;
+    }
+    return act;
+}
+
+// Pull result of v, with the vertex phase of round rn = round + 1 done on
+// the spot: the sources acc & ~vs are new at v; they join vis[v] and go to
+// nwn[v], the next pull's gather source.  v's rows are written here when
+// w.rows_in_pull is set, else by the next vertex phase (a streaming pass over
+// the frontier; which is faster depends on the graph, the autotuner
+// chooses).  A pull round writes no queue: the next vertex phase finds the
+// frontier in the bitmap.  Counts v and its arcs for the next direction
+// decision, notes its slots with new sources, and returns whether v joins
+// F_{rn}.
 template <int P>
 __device__ __forceinline__ bool pull_finish(const Wave& w, int32_t v, const uint64_t (&acc)[P], const uint64_t (&vs)[P],
-                                            uint32_t deg, unsigned long long& cnt, unsigned long long& sdeg) {
-    uint64_t nw[P], any = 0;
+                                            uint32_t deg, int rn, uint64_t* nwn, unsigned long long& cnt,
+                                            unsigned long long& sdeg, unsigned int& act) {
+    uint64_t nw[P], nv[P], any = 0;
 #pragma unroll
     for (int s = 0; s < P; ++s) {
         nw[s] = acc[s] & ~vs[s];
+        nv[s] = vs[s] | nw[s];
         any |= nw[s];
+        if (nw[s]) act |= 1u << s;
     }
-    if (any) {
-        store_words<P>(w.acc + (size_t)v * P, nw);
-        cnt += 1;
-        sdeg += deg;
-    }
-    return any != 0;
+    if (!any) return false;
+    store_words<P>(w.vis + (size_t)v * P, nv);
+    store_words<P>(nwn + (size_t)v * P, nw);
+    if (w.rows_in_pull) record_rows<P>(w, (uint32_t)v, nw, rn, w.slots);
+    cnt += 1;
+    sdeg += deg;
+    return true;
 }
 
 }  // namespace
@@ -369,8 +439,13 @@ __global__ void k_round_cond(Wave w, cudaGraphConditionalHandle h) {
 // Phase A: the vertex phase of round `round`, the direction decision and,
 // for a push round, the push work lists.  A small frontier is read from the
 // queue; a large one (qlen * dense_div > n) by scanning every vertex in
-// internal order for a non-zero acc block, which streams instead of
-// gathering.
+// internal order for its frontier bit, which streams instead of gathering.
+// When F_round was produced by a pull round, that pull already added
+// F_round's new sources to vis and left them in nw[round & 1] (pull_finish):
+// then this kernel records them in the rows unless the pull did
+// (rows_in_pull) and, for a push round, builds the push lists.  Otherwise (F_round pushed, or the sources) it takes the
+// new sources from acc, updates vis and the rows, and for a pull round stores
+// them in nw[round & 1] for the pull to gather.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     constexpr int EPT = Geo<P>::kEpt;
@@ -384,13 +459,15 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
     const bool pull = decide_pull(w, c);
-    const bool dense = c->dense || (w.dense_div > 0 && qlen * (unsigned long long)w.dense_div > (unsigned long long)w.n);
+    const bool fused = c->dense != 0;  // F_round came from a pull, which did its vertex phase
+    const bool dense = fused || (w.dense_div > 0 && qlen * (unsigned long long)w.dense_div > (unsigned long long)w.n);
     if (blockIdx.x == 0 && threadIdx.x == 0) c->mode = pull ? 1 : 0;
     if (threadIdx.x < w.nslots) ss[threadIdx.x] = w.slots[threadIdx.x];
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
     const uint32_t* q = (round & 1) ? w.q1 : w.q0;
     const uint32_t* fbr = (round & 1) ? w.fb1 : w.fb0;  // F_round, set by its producers
+    uint64_t* nwc = (round & 1) ? w.nw1 : w.nw0;        // F_round's new sources (pull gathers)
     {
         // F_{round+1}'s bitmap was last read in round - 1: clear it for this round's edge phase
         uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
@@ -398,6 +475,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
         for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads)
             fbn[i] = 0u;
     }
+    if (fused && pull && w.rows_in_pull) return;  // nothing left of F_round's vertex phase
     const unsigned long long span = dense ? (unsigned long long)w.n : qlen;
     const unsigned long long ntiles = (span + TILE - 1) / TILE;
     unsigned long long my_nf = 0;
@@ -418,72 +496,36 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             if (idx >= span) continue;
             if (dense && !((fbr[idx >> 5] >> (idx & 31)) & 1u)) continue;  // not in F_round
             const uint32_t u = dense ? (uint32_t)idx : q[idx];
-            uint64_t a[P], vs[P];
-            load_words<P>(w.acc + (size_t)u * P, a);
-            uint64_t anyacc = 0;
+            if (fused) {
+                // vis updated by the pull that produced F_round: record the rows
+                load_words<P>(nwc + (size_t)u * P, fw[r]);
+                if (!w.rows_in_pull) record_rows<P>(w, u, fw[r], round, ss);
+                if (pull) continue;  // the dense edge phase needs no work lists
+            } else {
+                uint64_t a[P], vs[P];
+                load_words<P>(w.acc + (size_t)u * P, a);
+                uint64_t anyacc = 0;
 #pragma unroll
-            for (int s = 0; s < P; ++s) anyacc |= a[s];
-            if (!anyacc) continue;  // not in F_round (dense scan), or nothing new
-            load_words<P>(w.vis + (size_t)u * P, vs);
-            uint64_t any = 0;
-#pragma unroll
-            for (int s = 0; s < P; ++s) {
-                fw[r][s] = a[s] & ~vs[s];
-                any |= fw[r][s];
-                vs[s] |= fw[r][s];
-            }
-            store_words<P>(w.vis + (size_t)u * P, vs);
-            zero_words<P>(w.acc + (size_t)u * P);
-            if (!any) continue;
-            if (w.dist_r) {
-                // the wave's internal rows of u: P Delta bytes, then each slot's
-                // d subset words contiguous (slot s at mr[s*d .. s*d + d))
-                uint8_t* dr = w.dist_r + (size_t)u * P;
-                uint64_t* mr = w.masks_r + (size_t)u * w.d * P;
-                uint16_t* wr = w.wmask_r + (size_t)u * P;
+                for (int s = 0; s < P; ++s) anyacc |= a[s];
+                if (!anyacc) continue;  // not in F_round (dense scan), or nothing new
+                load_words<P>(w.vis + (size_t)u * P, vs);
+                uint64_t any = 0;
 #pragma unroll
                 for (int s = 0; s < P; ++s) {
-                    if (!fw[r][s]) continue;
-                    const uint8_t dd = dr[s];
-                    int j;
-                    uint32_t wm;
-                    if (dd == 0xFF) {
-                        if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
-                        else dr[s] = (uint8_t)round;
-                        j = 0;
-                        // first visit of slot s: the rows are not cleared per wave, so
-                        // the written-word mask starts here (k_emit outputs 0 for a
-                        // word whose bit is clear, and ignores unreached slots)
-                        wm = 0;
-                    } else {
-                        j = round - (int)dd;
-                        wm = wr[s];
-                    }
-                    if (j < w.d) {
-                        mr[(size_t)s * w.d + j] = fw[r][s];
-                        wr[s] = (uint16_t)(wm | (1u << j));
-                    }
-                    else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
-                    my_active |= 1u << s;
+                    fw[r][s] = a[s] & ~vs[s];
+                    any |= fw[r][s];
+                    vs[s] |= fw[r][s];
                 }
-            } else {
-                // direct: one cluster, caller's ids, caller's arrays
-                const SlotDesc& S = ss[0];
-                const uint8_t dd = S.dist[u];
-                int j;
-                if (dd == 0xFF) {
-                    if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
-                    else S.dist[u] = (uint8_t)round;
-                    j = 0;
-                } else {
-                    j = round - (int)dd;
+                store_words<P>(w.vis + (size_t)u * P, vs);
+                zero_words<P>(w.acc + (size_t)u * P);
+                if (!any) continue;
+                my_active |= record_rows<P>(w, u, fw[r], round, ss);
+                my_nf += 1;
+                if (pull) {
+                    store_words<P>(nwc + (size_t)u * P, fw[r]);  // the gather source of this round's pull
+                    continue;  // the dense edge phase needs no work lists
                 }
-                if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = fw[r][0];
-                else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
-                my_active |= 1u;
             }
-            my_nf += 1;
-            if (pull) continue;  // the dense edge phase needs no work lists
             const int64_t o0 = w.off[u], o1 = w.off[u + 1];
             const int64_t deg = o1 - o0;
             if (deg == 0) continue;
@@ -527,6 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             }
         }
     }
+    if (fused) return;  // the pull counted F_round and its active slots
     const unsigned long long bnf = block_sum(my_nf, red);
     const unsigned int wa = __reduce_or_sync(0xffffffffu, my_active);
     if ((threadIdx.x & 31) == 0 && wa) atomicOr(&s_active, wa);
@@ -627,6 +670,12 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     }
 
     // ---- pull: dense pass over every vertex that can still gain sources.
+    // A vertex ORs the sources new at its frontier neighbours this round
+    // (nw[round & 1]; a neighbour's older sources are already in vis[v], and a
+    // non-frontier neighbour's entry holds sources of an earlier round, so
+    // both add nothing), then does its own vertex phase of round + 1 on the
+    // spot (pull_finish): vis is updated in place, which is safe because no
+    // pull reads another vertex's vis.
     // Degree classes are consecutive rank ranges: big [0, nb), mid [nb, nb + nm),
     // small [nb + nm, nb + nm + ns).
     const bool sparse_round = w.n_big_s >= 0 && qlen * 32 < (unsigned long long)w.n;
@@ -636,10 +685,16 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     const uint64_t* pieces = sparse_round ? w.pull_pieces_s : w.pull_pieces;
     const int64_t npieces = sparse_round ? w.n_pull_pieces_s : w.n_pull_pieces;
     const unsigned int active = c->slot_active;
+    const uint64_t* nwc = (round & 1) ? w.nw1 : w.nw0;  // gather source: F_round's new sources
+    uint64_t* nwn = (round & 1) ? w.nw0 : w.nw1;        // F_{round+1}'s, written by pull_finish
+    const int rn = round + 1;
     unsigned long long my_cnt = 0, my_sdeg = 0;
+    unsigned int my_act = 0;
     const uint64_t* all = sall;  // ALL of each slot, read from shared memory where needed
     // high-degree vertices: their lists are cut into kBigDeg-arc pieces that
-    // all CTAs take from a counter; each piece ORs its part into acc[v]
+    // all CTAs take from a counter; each piece ORs its part into acc[v], and
+    // the last piece of v to finish (a per-vertex counter, reset by it) does
+    // v's vertex phase
     for (;;) {
         if (threadIdx.x == 0) s_work = atomicAdd(&c->piece_ctr, 1u);
         __syncthreads();
@@ -656,7 +711,8 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         if (threadIdx.x == 0) {
             uint64_t vs[P], ac[P];
             load_words<P>(w.vis + (size_t)v * P, vs);
-            load_words<P>(w.acc + (size_t)v * P, ac);
+#pragma unroll
+            for (int s = 0; s < P; ++s) ac[s] = __ldcg(reinterpret_cast<const unsigned long long*>(w.acc + (size_t)v * P + s));
 #pragma unroll
             for (int s = 0; s < P; ++s) sor[1][s] = vs[s] | ac[s];
         }
@@ -666,45 +722,49 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         for (int s = 0; s < P; ++s) seen[s] = sor[1][s];
         __syncthreads();
         const unsigned int um = unfinished<P>(seen, all, active);
-        if (!um) continue;  // uniform: seen comes from shared memory
         uint64_t acc[P];
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] = 0;
-        for (int64_t b0 = a0; b0 < a1; b0 += Gath<P>::G * kThreads) {
-            gather<P>(w, fb, w.adj, b0 + threadIdx.x, kThreads, a1, acc);
+        if (um) {  // uniform: seen comes from shared memory
+            for (int64_t b0 = a0; b0 < a1; b0 += Gath<P>::G * kThreads) {
+                gather<P>(nwc, fb, w.adj, b0 + threadIdx.x, kThreads, a1, acc);
 #pragma unroll
-            for (int s = 0; s < P; ++s) {
-                const uint64_t wa = warp_or(acc[s]);
-                if ((threadIdx.x & 31) == 0) sor[threadIdx.x >> 5][s] = wa;
-            }
-            __syncthreads();
-            if (threadIdx.x < P) {
-                uint64_t x = 0;
-                for (int k = 0; k < kWarps; ++k) x |= sor[k][threadIdx.x];
-                sor[0][threadIdx.x] = x;
-            }
-            __syncthreads();
+                for (int s = 0; s < P; ++s) {
+                    const uint64_t wa = warp_or(acc[s]);
+                    if ((threadIdx.x & 31) == 0) sor[threadIdx.x >> 5][s] = wa;
+                }
+                __syncthreads();
+                if (threadIdx.x < P) {
+                    uint64_t x = 0;
+                    for (int k = 0; k < kWarps; ++k) x |= sor[k][threadIdx.x];
+                    sor[0][threadIdx.x] = x;
+                }
+                __syncthreads();
 #pragma unroll
-            for (int s = 0; s < P; ++s) acc[s] = sor[0][s];
-            __syncthreads();
-            if (missing_bits<P>(acc, seen, all, um) == 0) break;
+                for (int s = 0; s < P; ++s) acc[s] = sor[0][s];
+                __syncthreads();
+                if (missing_bits<P>(acc, seen, all, um) == 0) break;
+            }
         }
         if (threadIdx.x == 0) {
-            bool claim = false;
 #pragma unroll
             for (int s = 0; s < P; ++s) {
-                const uint64_t nb = acc[s] & ~seen[s];
-                if (nb) {
-                    const unsigned long long old =
-                        atomicOr(reinterpret_cast<unsigned long long*>(w.acc + (size_t)v * P + s), (unsigned long long)nb);
-                    claim |= (old == 0ull);
-                }
+                const uint64_t nb_ = acc[s] & ~seen[s];
+                if (nb_) atomicOr(reinterpret_cast<unsigned long long*>(w.acc + (size_t)v * P + s), (unsigned long long)nb_);
             }
-            // the first piece to make acc[v] non-zero counts v once for F_{round+1}
-            if (claim && atomicExch(w.rq + v, stamp) != stamp) {
-                my_cnt += 1;
-                my_sdeg += (unsigned long long)(o1 - o0);
-                atomicOr(fbn + (v >> 5), 1u << (v & 31));
+            __threadfence();  // this piece's ORs before its count
+            const unsigned int npc = (unsigned int)((o1 - o0 + kBigDeg - 1) / kBigDeg);
+            if (atomicAdd(w.piece_cnt + v, 1u) == npc - 1) {
+                // every piece of v has ORed its part: v's vertex phase of round + 1
+                __threadfence();
+                w.piece_cnt[v] = 0u;
+                uint64_t vs[P], ac[P];
+                load_words<P>(w.vis + (size_t)v * P, vs);
+#pragma unroll
+                for (int s = 0; s < P; ++s) ac[s] = __ldcg(reinterpret_cast<const unsigned long long*>(w.acc + (size_t)v * P + s));
+                zero_words<P>(w.acc + (size_t)v * P);
+                if (pull_finish<P>(w, v, ac, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act))
+                    atomicOr(fbn + (v >> 5), 1u << (v & 31));
             }
         }
     }
@@ -724,12 +784,12 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
 #pragma unroll
         for (int s = 0; s < P; ++s) acc[s] = 0;
         for (int64_t b0 = o0; b0 < o1; b0 += 32 * Gath<P>::G) {
-            gather<P>(w, fb, w.adj, b0 + lane, 32, o1, acc);
+            gather<P>(nwc, fb, w.adj, b0 + lane, 32, o1, acc);
 #pragma unroll
             for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
             if (missing_bits<P>(acc, vs, all, um) == 0) break;
         }
-        if (lane == 0 && pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg))
+        if (lane == 0 && pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act))
             atomicOr(fbn + (v >> 5), 1u << (v & 31));
     }
     // low-degree vertices: a warp takes 32 consecutive ones, whose lists are
@@ -757,10 +817,10 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
 #pragma unroll
                 for (int s = 0; s < P; ++s) acc[s] = 0;
                 for (int64_t e = o0; e < o1; e += Gath<P>::G) {
-                    gather<P>(w, fb, wadj - lo, e, 1, o1, acc);
+                    gather<P>(nwc, fb, wadj - lo, e, 1, o1, acc);
                     if (missing_bits<P>(acc, vs, all, um) == 0) break;
                 }
-                joined = pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), my_cnt, my_sdeg);
+                joined = pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act);
             }
         }
         // the 32 vertices are consecutive: their bits span at most two bitmap words
@@ -773,13 +833,22 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         }
         __syncwarp();
     }
-    // publish the next frontier's size and arcs: one atomic pair per CTA
+    // publish the next frontier's size, arcs and active slots: one atomic each per CTA
     __shared__ unsigned long long red[kWarps];
+    __shared__ unsigned int s_act;
+    if (threadIdx.x == 0) s_act = 0;
     const unsigned long long bc = block_sum(my_cnt, red);
     const unsigned long long bs = block_sum(my_sdeg, red);
+    const unsigned int wact = __reduce_or_sync(0xffffffffu, my_act);
+    if (lane == 0 && wact) atomicOr(&s_act, wact);
+    __syncthreads();
     if (threadIdx.x == 0) {
-        if (bc) atomicAdd(&cn->qlen, bc);
+        if (bc) {
+            atomicAdd(&cn->qlen, bc);
+            atomicAdd(&cn->nf, bc);
+        }
         if (bs) atomicAdd(&cn->sdeg, bs);
+        if (s_act) atomicOr(&cn->slot_active, s_act);
         if (blockIdx.x == 0) cn->dense = 1;
     }
 }
@@ -987,6 +1056,8 @@ struct cbfs_graph_s {
     int cap_slots = 0;
     uint64_t* vis = nullptr;
     uint64_t* acc = nullptr;
+    uint64_t* nw = nullptr;        // nw0 | nw1, [2][n][P]
+    uint32_t* piece_cnt = nullptr;
     uint32_t* rq = nullptr;
     uint32_t* q0 = nullptr;
     uint32_t* q1 = nullptr;
@@ -1090,6 +1161,8 @@ void dev_free(T*& p) {
 void free_scratch(cbfs_graph_s* g) {
     dev_free(g->vis);
     dev_free(g->acc);
+    dev_free(g->nw);
+    dev_free(g->piece_cnt);
     dev_free(g->rq);
     dev_free(g->q0);
     dev_free(g->q1);
@@ -1115,6 +1188,10 @@ int ensure_scratch(cbfs_graph_s* g, int P) {
     int rc = CBFS_OK;
     if (!rc) rc = dev_alloc(&g->vis, z.state);
     if (!rc) rc = dev_alloc(&g->acc, z.state);
+    if (!rc) rc = dev_alloc(&g->nw, 2 * z.state);
+    if (!rc) rc = dev_alloc(&g->piece_cnt, z.queue);
+    if (!rc && cudaMemset(g->piece_cnt, 0, sizeof(uint32_t) * (size_t)std::max<int64_t>(z.queue, 1)) != cudaSuccess)
+        rc = CBFS_E_CUDA;
     if (!rc) rc = dev_alloc(&g->rq, z.queue);
     if (!rc) rc = dev_alloc(&g->q0, z.queue);
     if (!rc) rc = dev_alloc(&g->q1, z.queue);
@@ -1247,6 +1324,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         const int cnt = (int)(seed_off[wv + 1] - seed_off[wv]);
         e = cudaMemsetAsync(w.vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.nw0, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.rq, 0, sizeof(uint32_t) * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.fb0, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.dist_r, 0xFF, (size_t)P * (size_t)n, cs);
@@ -1636,6 +1714,9 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.P = P;
     w.vis = g->vis;
     w.acc = g->acc;
+    w.nw0 = g->nw;
+    w.nw1 = g->nw + (size_t)P * (size_t)n;
+    w.piece_cnt = g->piece_cnt;
     w.rq = g->rq;
     w.q0 = g->q0;
     w.q1 = g->q1;
@@ -1670,6 +1751,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.wmask_r = g->wmask_r;
     w.masks_r = g->masks_r;
     w.dense_div = dense_div;
+    w.rows_in_pull = (tune && tune->rows_in_pull > 0) ? 1 : 0;
 
     // Graph mode (device outputs): the call runs as one cached CUDA graph per
     // call shape whose rounds loop on the device, and is stream-ordered: the
@@ -1748,6 +1830,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         w.slots = g->slots + (size_t)wv * P;
         CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
+        CK(cudaMemsetAsync(g->nw, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->rq, 0, sizeof(uint32_t) * (size_t)n, st));
         CK(cudaMemsetAsync(g->fb, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, st));
         CK(cudaMemsetAsync(g->dist_r, 0xFF, (size_t)P * (size_t)n, st));

@@ -81,6 +81,10 @@ struct Wave {
     const SlotDesc* slots;  // device [nslots]
     uint64_t* vis;          // [n][P]
     uint64_t* acc;          // [n][P]
+    uint64_t* nw0;          // [n][P] sources new at v in round i, for i even / odd: written by
+    uint64_t* nw1;          //   the vertex phase of v (in phase A, or in the pull of round i-1)
+                            //   and gathered by the pull of round i; cleared per wave
+    uint32_t* piece_cnt;    // [n] pull pieces of a hub done this round (the last one resets it)
     uint32_t* rq;           // [n] queue claim stamps: F_i holds v iff rq[v] was set to i+1
     uint32_t* q0;           // frontier queues of vertex ids
     uint32_t* q1;
@@ -111,6 +115,8 @@ struct Wave {
     uint16_t* wmask_r;      // [n][P] bit j: masks_r word j of the slot was written in this
                             // wave (started at the slot's first visit; never cleared)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
+    int rows_in_pull;       // 1: a pull records the rows of the vertices it finishes; 0: the
+                            //    next vertex phase does
     int* round_dev;         // graph mode: the current round lives here (nullptr: kernel argument)
     unsigned long long* iters;  // graph mode: rounds executed (for the launch accounting)
     int* status;
