@@ -460,7 +460,7 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
         n = g.n
         # this graph's own switch factor, clusters per wave and degree classes
         tn = tune.autotune(g, clusters, d, sample=per_launch, key_extra=f"grid-{side}-{tune.signature(off)}")
-        tset = {k: tn.get(k, 0) for k in ("pull_alpha", "slots", "small_deg", "mid_deg", "rows_in_pull")}
+        tset = {k: tn.get(k, 0) for k in ("pull_alpha", "slots", "small_deg", "mid_deg", "fused_pull")}
         dist = torch.empty((per_launch, n), dtype=torch.uint8, device="cuda")
         masks = torch.empty((per_launch, d, n), dtype=torch.int64, device="cuda")
         total_ms, A, V, src_edges, rounds = 0.0, 0, 0, 0, 0
@@ -682,7 +682,7 @@ def run_cbfs(args, ws, rank, local):
     else:
         tn = tune.autotune(g, clusters, d, key_extra=f"rmat-s{args.scale}-{tune.signature(off)}")
     tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"], "small_deg": tn.get("small_deg", 0),
-            "mid_deg": tn.get("mid_deg", 0), "rows_in_pull": tn.get("rows_in_pull", 0)}
+            "mid_deg": tn.get("mid_deg", 0), "fused_pull": tn.get("fused_pull", 0)}
     dist = torch.empty((C, n), dtype=torch.uint8, device=dev)
     masks = torch.empty((C, d, n), dtype=torch.int64, device=dev)
     L = cbfs.Labels(n, C, d)

@@ -111,13 +111,13 @@ typedef struct cbfs_tune_s {
        early), 1 = in call order.  Host outputs and label stores always use
        call order. */
     int wave_order;
-    /* a pull round adds each vertex's new sources to its state on the spot;
-       their record in the vertex's output rows is written by the pull itself
-       (1) or by the next round's vertex phase, a streaming pass over the
-       frontier (0, the default).  Graphs with locality in their vertex order
-       (a road grid) gain from 1, power-law graphs from 0; the autotuner
-       tries both. */
-    int rows_in_pull;
+    /* != 0: a pull round also does the vertex phase of the next round for
+       the vertices it finishes (their state, output rows and the sources new
+       at them, which the next pull gathers), saving a pass over the
+       frontier.  Graphs whose clusters' frontiers rarely meet in time (a
+       road grid) gain; on power-law graphs the plain pull is faster.  0 (the
+       default) = plain; the autotuner tries both. */
+    int fused_pull;
 } cbfs_tune_t;
 
 /* Work counters of one cluster's traversal (Theorem 1). */

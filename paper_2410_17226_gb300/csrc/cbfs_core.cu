@@ -306,17 +306,21 @@ __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, c
                 if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
                 else dr[s] = (uint8_t)round;
                 j = 0;
-                // first visit of slot s: the rows are not cleared per wave, so
-                // the written-word mask starts here (k_emit outputs 0 for a
-                // word whose bit is clear, and ignores unreached slots)
+                // first visit of slot s: the rows are not cleared per wave.  A
+                // slot's block of at most kZeroWords words (one sector) is
+                // zeroed here; longer blocks get a written-word mask instead
+                // (k_emit outputs 0 for a word whose bit is clear), which
+                // avoids writing d words at the first visit
                 wm = 0;
+                if (w.d <= kZeroWords)
+                    for (int jj = 1; jj < w.d; ++jj) mr[(size_t)s * w.d + jj] = 0ull;
             } else {
                 j = round - (int)dd;
-                wm = wr[s];
+                wm = w.d > kZeroWords ? wr[s] : 0u;
             }
             if (j < w.d) {
                 mr[(size_t)s * w.d + j] = fw[s];
-                wr[s] = (uint16_t)(wm | (1u << j));
+                if (w.d > kZeroWords) wr[s] = (uint16_t)(wm | (1u << j));
             } else if (j > w.d) {
                 set_status(w.status, CBFS_E_DIAMETER);
             }
@@ -341,31 +345,36 @@ __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, c
     return act;
 }
 
-// Pull result of v, with the vertex phase of round rn = round + 1 done on
-// the spot: the sources acc & ~vs are new at v; they join vis[v] and go to
-// nwn[v], the next pull's gather source.  v's rows are written here when
-// w.rows_in_pull is set, else by the next vertex phase (a streaming pass over
-// the frontier; which is faster depends on the graph, the autotuner
-// chooses).  A pull round writes no queue: the next vertex phase finds the
-// frontier in the bitmap.  Counts v and its arcs for the next direction
-// decision, notes its slots with new sources, and returns whether v joins
-// F_{rn}.
-template <int P>
+// Pull result of v.  Fused (FUSE, the call's fused_pull): the vertex phase of
+// round rn = round + 1 is done on the spot -- the sources acc & ~vs are new
+// at v, they join vis[v], go to v's rows and to nwn[v], the next pull's
+// gather source.  Plain: the new sources are stored in acc[v] for the next
+// vertex phase.  A pull round writes no queue: the next vertex phase finds
+// the frontier in the bitmap.  Counts v and its arcs for the next direction
+// decision, notes its slots with new sources (fused), and returns whether v
+// joins F_{rn}.
+template <int P, bool FUSE>
 __device__ __forceinline__ bool pull_finish(const Wave& w, int32_t v, const uint64_t (&acc)[P], const uint64_t (&vs)[P],
                                             uint32_t deg, int rn, uint64_t* nwn, unsigned long long& cnt,
                                             unsigned long long& sdeg, unsigned int& act) {
-    uint64_t nw[P], nv[P], any = 0;
+    uint64_t nw[P], any = 0;
 #pragma unroll
     for (int s = 0; s < P; ++s) {
         nw[s] = acc[s] & ~vs[s];
-        nv[s] = vs[s] | nw[s];
         any |= nw[s];
-        if (nw[s]) act |= 1u << s;
+        if (FUSE && nw[s]) act |= 1u << s;
     }
     if (!any) return false;
-    store_words<P>(w.vis + (size_t)v * P, nv);
-    store_words<P>(nwn + (size_t)v * P, nw);
-    if (w.rows_in_pull) record_rows<P>(w, (uint32_t)v, nw, rn, w.slots);
+    if (FUSE) {
+        uint64_t nv[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) nv[s] = vs[s] | nw[s];
+        store_words<P>(w.vis + (size_t)v * P, nv);
+        store_words<P>(nwn + (size_t)v * P, nw);
+        record_rows<P>(w, (uint32_t)v, nw, rn, w.slots);
+    } else {
+        store_words<P>(w.acc + (size_t)v * P, nw);
+    }
     cnt += 1;
     sdeg += deg;
     return true;
@@ -440,12 +449,12 @@ __global__ void k_round_cond(Wave w, cudaGraphConditionalHandle h) {
 // for a push round, the push work lists.  A small frontier is read from the
 // queue; a large one (qlen * dense_div > n) by scanning every vertex in
 // internal order for its frontier bit, which streams instead of gathering.
-// When F_round was produced by a pull round, that pull already added
-// F_round's new sources to vis and left them in nw[round & 1] (pull_finish):
-// then this kernel records them in the rows unless the pull did
-// (rows_in_pull) and, for a push round, builds the push lists.  Otherwise (F_round pushed, or the sources) it takes the
-// new sources from acc, updates vis and the rows, and for a pull round stores
-// them in nw[round & 1] for the pull to gather.
+// When F_round was produced by a fused pull, that pull already did F_round's
+// vertex phase and left its new sources in nw[round & 1]: then this kernel
+// only builds the push lists (push round) or returns (pull round).
+// Otherwise (F_round pushed or plainly pulled, or the sources) it takes the
+// new sources from acc, updates vis and the rows, and before a fused pull
+// stores them in nw[round & 1] for the pull to gather.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     constexpr int EPT = Geo<P>::kEpt;
@@ -459,8 +468,10 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     const unsigned long long qlen = c->qlen;
     if (qlen == 0) return;
     const bool pull = decide_pull(w, c);
-    const bool fused = c->dense != 0;  // F_round came from a pull, which did its vertex phase
-    const bool dense = fused || (w.dense_div > 0 && qlen * (unsigned long long)w.dense_div > (unsigned long long)w.n);
+    const bool fused = c->fused != 0;  // F_round came from a pull that did its set update
+    // this round's pull gathers nw when pulls are fused
+    const bool pull_fused = pull && w.fused_pull;
+    const bool dense = c->dense || (w.dense_div > 0 && qlen * (unsigned long long)w.dense_div > (unsigned long long)w.n);
     if (blockIdx.x == 0 && threadIdx.x == 0) c->mode = pull ? 1 : 0;
     if (threadIdx.x < w.nslots) ss[threadIdx.x] = w.slots[threadIdx.x];
     if (threadIdx.x == 0) s_active = 0;
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
         for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads)
             fbn[i] = 0u;
     }
-    if (fused && pull && w.rows_in_pull) return;  // nothing left of F_round's vertex phase
+    if (fused && pull) return;  // nothing left of F_round's vertex phase
     const unsigned long long span = dense ? (unsigned long long)w.n : qlen;
     const unsigned long long ntiles = (span + TILE - 1) / TILE;
     unsigned long long my_nf = 0;
@@ -499,7 +510,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             if (fused) {
                 // vis updated by the pull that produced F_round: record the rows
                 load_words<P>(nwc + (size_t)u * P, fw[r]);
-                if (!w.rows_in_pull) record_rows<P>(w, u, fw[r], round, ss);
+                // (the fused pull recorded the rows too)
                 if (pull) continue;  // the dense edge phase needs no work lists
             } else {
                 uint64_t a[P], vs[P];
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                 my_active |= record_rows<P>(w, u, fw[r], round, ss);
                 my_nf += 1;
                 if (pull) {
-                    store_words<P>(nwc + (size_t)u * P, fw[r]);  // the gather source of this round's pull
+                    if (pull_fused) store_words<P>(nwc + (size_t)u * P, fw[r]);  // the pull's gather source
                     continue;  // the dense edge phase needs no work lists
                 }
             }
@@ -580,8 +591,227 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     }
 }
 
+// The pull (dense edge phase) of round `round`.  FUSE: the round also does
+// the set update of round + 1 for the vertices it finishes (see k_phase_b);
+// otherwise it leaves their new sources in acc.  Two instantiations keep the
+// plain pull's code and registers as they are without the fused work.
+template <int P, bool FUSE>
+__device__ __forceinline__ void pull_round(const Wave& w, RoundCtl* c, RoundCtl* cn, int round,
+                                           unsigned long long qlen, const uint32_t* fb, uint32_t* fbn, uint32_t stamp,
+                                           const uint64_t* sall, unsigned int* s_work_p, uint64_t (*sor)[P],
+                                           int32_t (*sadj)[32 * kPullSmall]) {
+    // ---- pull: dense pass over every vertex that can still gain sources.
+    // Plain: every vertex ORs the vis blocks of its frontier neighbours and
+    // leaves the new part in acc for the next vertex phase.  Fused: it ORs the
+    // sources new at its neighbours this round instead (nw[round & 1]; a
+    // frontier neighbour's older sources are already in vis[v], and a
+    // non-frontier neighbour's entry -- read without the bitmap test when the
+    // frontier is dense; cleared per wave -- holds sources of an earlier
+    // round, so neither adds anything), then does v's vertex phase of
+    // round + 1 on the spot (pull_finish): vis is updated in place, which is
+    // safe because a fused round reads no other vertex's vis.  Fused pulls
+    // save the next vertex phase's pass over the frontier; graphs whose
+    // clusters' frontiers rarely meet (a road grid) gain, power-law graphs do
+    // not: the call's fused_pull chooses (autotuned).
+    // Degree classes are consecutive rank ranges: big [0, nb), mid [nb, nb + nm),
+    // small [nb + nm, nb + nm + ns).
+    const bool sparse_round = w.n_big_s >= 0 && qlen * 32 < (unsigned long long)w.n;
+    const int64_t nb = sparse_round ? w.n_big_s : w.n_big;
+    const int64_t nm = sparse_round ? w.n_mid_s : w.n_mid;
+    const int64_t ns = sparse_round ? w.n_small_s : w.n_small;
+    const uint64_t* pieces = sparse_round ? w.pull_pieces_s : w.pull_pieces;
+    const int64_t npieces = sparse_round ? w.n_pull_pieces_s : w.n_pull_pieces;
+    const unsigned int active = c->slot_active;
+    const uint64_t* gsrc = FUSE ? ((round & 1) ? w.nw1 : w.nw0) : w.vis;  // gather source
+    uint64_t* nwn = (round & 1) ? w.nw0 : w.nw1;  // F_{round+1}'s new sources, written by pull_finish
+    const int rn = round + 1;
+    unsigned long long my_cnt = 0, my_sdeg = 0;
+    unsigned int my_act = 0;
+    const uint64_t* all = sall;  // ALL of each slot, read from shared memory where needed
+    unsigned int& s_work = *s_work_p;
+    // high-degree vertices: their lists are cut into kBigDeg-arc pieces that
+    // all CTAs take from a counter; each piece ORs its part into acc[v].
+    // Fused, the last piece of v to finish (a per-vertex counter, reset by
+    // it) does v's set update; plain, the first piece to make acc[v] non-zero
+    // counts v and acc[v] goes to the next vertex phase
+    for (;;) {
+        if (threadIdx.x == 0) s_work = atomicAdd(&c->piece_ctr, 1u);
+        __syncthreads();
+        const unsigned int p = s_work;
+        __syncthreads();
+        if (p >= npieces) break;
+        const uint64_t pc = pieces[p];
+        const int32_t v = (int32_t)(pc >> 32);
+        const int64_t o0 = w.off[v], o1 = w.off[v + 1];
+        const int64_t a0 = o0 + (int64_t)(uint32_t)pc * kBigDeg;
+        const int64_t a1 = min(o1, a0 + kBigDeg);
+        // acc[v] may be growing under other pieces: one thread reads it so that
+        // every thread of the block decides on the same snapshot
+        if (threadIdx.x == 0) {
+            uint64_t vs[P], ac[P];
+            load_words<P>(w.vis + (size_t)v * P, vs);
+#pragma unroll
+            for (int s = 0; s < P; ++s) ac[s] = __ldcg(reinterpret_cast<const unsigned long long*>(w.acc + (size_t)v * P + s));
+#pragma unroll
+            for (int s = 0; s < P; ++s) sor[1][s] = vs[s] | ac[s];
+        }
+        __syncthreads();
+        uint64_t seen[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) seen[s] = sor[1][s];
+        __syncthreads();
+        const unsigned int um = unfinished<P>(seen, all, active);
+        uint64_t acc[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) acc[s] = 0;
+        if (!FUSE && !um) continue;  // uniform: seen comes from shared memory
+        if (um) {
+            for (int64_t b0 = a0; b0 < a1; b0 += Gath<P>::G * kThreads) {
+                gather<P>(gsrc, fb, w.adj, b0 + threadIdx.x, kThreads, a1, acc);
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    const uint64_t wa = warp_or(acc[s]);
+                    if ((threadIdx.x & 31) == 0) sor[threadIdx.x >> 5][s] = wa;
+                }
+                __syncthreads();
+                if (threadIdx.x < P) {
+                    uint64_t x = 0;
+                    for (int k = 0; k < kWarps; ++k) x |= sor[k][threadIdx.x];
+                    sor[0][threadIdx.x] = x;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int s = 0; s < P; ++s) acc[s] = sor[0][s];
+                __syncthreads();
+                if (missing_bits<P>(acc, seen, all, um) == 0) break;
+            }
+        }
+        if (threadIdx.x == 0) {
+            bool claim = false;
+#pragma unroll
+            for (int s = 0; s < P; ++s) {
+                const uint64_t nb_ = acc[s] & ~seen[s];
+                if (nb_) {
+                    const unsigned long long old =
+                        atomicOr(reinterpret_cast<unsigned long long*>(w.acc + (size_t)v * P + s), (unsigned long long)nb_);
+                    claim |= (old == 0ull);
+                }
+            }
+            if (FUSE) {
+                __threadfence();  // this piece's ORs before its count
+                const unsigned int npc = (unsigned int)((o1 - o0 + kBigDeg - 1) / kBigDeg);
+                if (atomicAdd(w.piece_cnt + v, 1u) == npc - 1) {
+                    // every piece of v has ORed its part into acc[v]: v's set update of round + 1
+                    __threadfence();
+                    w.piece_cnt[v] = 0u;
+                    uint64_t vs[P], ac[P];
+                    load_words<P>(w.vis + (size_t)v * P, vs);
+#pragma unroll
+                    for (int s = 0; s < P; ++s)
+                        ac[s] = __ldcg(reinterpret_cast<const unsigned long long*>(w.acc + (size_t)v * P + s));
+                    zero_words<P>(w.acc + (size_t)v * P);
+                    if (pull_finish<P, true>(w, v, ac, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act))
+                        atomicOr(fbn + (v >> 5), 1u << (v & 31));
+                }
+            } else if (claim && atomicExch(w.rq + v, stamp) != stamp) {
+                // the first piece to make acc[v] non-zero counts v once for F_{round+1};
+                // acc[v] stays for the next vertex phase
+                my_cnt += 1;
+                my_sdeg += (unsigned long long)(o1 - o0);
+                atomicOr(fbn + (v >> 5), 1u << (v & 31));
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nw_total = ((int64_t)gridDim.x * kThreads) >> 5;
+    // warp per mid-degree vertex
+    for (int64_t i = gw; i < nm; i += nw_total) {
+        const int32_t v = (int32_t)(nb + i);
+        uint64_t vs[P];
+        load_words<P>(w.vis + (size_t)v * P, vs);
+        const unsigned int um = unfinished<P>(vs, all, active);
+        if (!um) continue;
+        const int64_t o0 = w.off[v], o1 = w.off[v + 1];
+        uint64_t acc[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) acc[s] = 0;
+        for (int64_t b0 = o0; b0 < o1; b0 += 32 * Gath<P>::G) {
+            gather<P>(gsrc, fb, w.adj, b0 + lane, 32, o1, acc);
+#pragma unroll
+            for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
+            if (missing_bits<P>(acc, vs, all, um) == 0) break;
+        }
+        if (lane == 0 && pull_finish<P, FUSE>(w, v, acc, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act))
+            atomicOr(fbn + (v >> 5), 1u << (v & 31));
+    }
+    // low-degree vertices: a warp takes 32 consecutive ones, whose lists are
+    // consecutive in the internal order, stages them in shared memory with
+    // coalesced loads, then each lane scans its own list
+    int32_t* wadj = sadj[wib];
+    const int64_t small0 = nb + nm;
+    for (int64_t g0 = gw * 32; g0 < ns; g0 += nw_total * 32) {
+        const int64_t i = g0 + lane;
+        const bool has = i < ns;
+        const int32_t v = has ? (int32_t)(small0 + i) : 0;
+        const int64_t o0 = has ? w.off[v] : 0, o1 = has ? w.off[v + 1] : 0;
+        const int last = (int)((ns - 1 - g0) < 31 ? (ns - 1 - g0) : 31);
+        const int64_t lo = __shfl_sync(0xffffffffu, o0, 0);
+        const int64_t hi = __shfl_sync(0xffffffffu, o1, last);
+        for (int64_t x = lo + lane; x < hi; x += 32) wadj[x - lo] = w.adj[x];
+        __syncwarp();
+        bool joined = false;
+        if (has) {
+            uint64_t vs[P];
+            load_words<P>(w.vis + (size_t)v * P, vs);
+            const unsigned int um = unfinished<P>(vs, all, active);
+            if (um) {
+                uint64_t acc[P];
+#pragma unroll
+                for (int s = 0; s < P; ++s) acc[s] = 0;
+                for (int64_t e = o0; e < o1; e += Gath<P>::G) {
+                    gather<P>(gsrc, fb, wadj - lo, e, 1, o1, acc);
+                    if (missing_bits<P>(acc, vs, all, um) == 0) break;
+                }
+                joined = pull_finish<P, FUSE>(w, v, acc, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act);
+            }
+        }
+        // the 32 vertices are consecutive: their bits span at most two bitmap words
+        const unsigned int jm = __ballot_sync(0xffffffffu, joined);
+        if (lane == 0 && jm) {
+            const int32_t v0 = (int32_t)(small0 + g0);
+            const int sh = v0 & 31;
+            atomicOr(fbn + (v0 >> 5), jm << sh);
+            if (sh && (jm >> (32 - sh))) atomicOr(fbn + (v0 >> 5) + 1, jm >> (32 - sh));
+        }
+        __syncwarp();
+    }
+    // publish the next frontier's size, arcs and active slots: one atomic each per CTA
+    __shared__ unsigned long long red[kWarps];
+    __shared__ unsigned int s_act;
+    if (threadIdx.x == 0) s_act = 0;
+    const unsigned long long bc = block_sum(my_cnt, red);
+    const unsigned long long bs = block_sum(my_sdeg, red);
+    const unsigned int wact = __reduce_or_sync(0xffffffffu, my_act);
+    if (lane == 0 && wact) atomicOr(&s_act, wact);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (bc) {
+            atomicAdd(&cn->qlen, bc);
+            atomicAdd(&cn->nf, bc);
+        }
+        if (bs) atomicAdd(&cn->sdeg, bs);
+        if (s_act) atomicOr(&cn->slot_active, s_act);
+        if (blockIdx.x == 0) {
+            cn->dense = 1;
+            cn->fused = FUSE ? 1 : 0;
+        }
+    }
+}
+
 // Phase B: the edge phase of round `round` in the direction phase A chose.
-template <int P>
+template <int P, bool FUSE>
 __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, int round) {
     constexpr int TILE = Geo<P>::kTile;
     // push and pull never run in the same launch: their staging buffers overlap
@@ -669,188 +899,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
         return;
     }
 
-    // ---- pull: dense pass over every vertex that can still gain sources.
-    // A vertex ORs the sources new at its frontier neighbours this round
-    // (nw[round & 1]; a neighbour's older sources are already in vis[v], and a
-    // non-frontier neighbour's entry holds sources of an earlier round, so
-    // both add nothing), then does its own vertex phase of round + 1 on the
-    // spot (pull_finish): vis is updated in place, which is safe because no
-    // pull reads another vertex's vis.
-    // Degree classes are consecutive rank ranges: big [0, nb), mid [nb, nb + nm),
-    // small [nb + nm, nb + nm + ns).
-    const bool sparse_round = w.n_big_s >= 0 && qlen * 32 < (unsigned long long)w.n;
-    const int64_t nb = sparse_round ? w.n_big_s : w.n_big;
-    const int64_t nm = sparse_round ? w.n_mid_s : w.n_mid;
-    const int64_t ns = sparse_round ? w.n_small_s : w.n_small;
-    const uint64_t* pieces = sparse_round ? w.pull_pieces_s : w.pull_pieces;
-    const int64_t npieces = sparse_round ? w.n_pull_pieces_s : w.n_pull_pieces;
-    const unsigned int active = c->slot_active;
-    const uint64_t* nwc = (round & 1) ? w.nw1 : w.nw0;  // gather source: F_round's new sources
-    uint64_t* nwn = (round & 1) ? w.nw0 : w.nw1;        // F_{round+1}'s, written by pull_finish
-    const int rn = round + 1;
-    unsigned long long my_cnt = 0, my_sdeg = 0;
-    unsigned int my_act = 0;
-    const uint64_t* all = sall;  // ALL of each slot, read from shared memory where needed
-    // high-degree vertices: their lists are cut into kBigDeg-arc pieces that
-    // all CTAs take from a counter; each piece ORs its part into acc[v], and
-    // the last piece of v to finish (a per-vertex counter, reset by it) does
-    // v's vertex phase
-    for (;;) {
-        if (threadIdx.x == 0) s_work = atomicAdd(&c->piece_ctr, 1u);
-        __syncthreads();
-        const unsigned int p = s_work;
-        __syncthreads();
-        if (p >= npieces) break;
-        const uint64_t pc = pieces[p];
-        const int32_t v = (int32_t)(pc >> 32);
-        const int64_t o0 = w.off[v], o1 = w.off[v + 1];
-        const int64_t a0 = o0 + (int64_t)(uint32_t)pc * kBigDeg;
-        const int64_t a1 = min(o1, a0 + kBigDeg);
-        // acc[v] may be growing under other pieces: one thread reads it so that
-        // every thread of the block decides on the same snapshot
-        if (threadIdx.x == 0) {
-            uint64_t vs[P], ac[P];
-            load_words<P>(w.vis + (size_t)v * P, vs);
-#pragma unroll
-            for (int s = 0; s < P; ++s) ac[s] = __ldcg(reinterpret_cast<const unsigned long long*>(w.acc + (size_t)v * P + s));
-#pragma unroll
-            for (int s = 0; s < P; ++s) sor[1][s] = vs[s] | ac[s];
-        }
-        __syncthreads();
-        uint64_t seen[P];
-#pragma unroll
-        for (int s = 0; s < P; ++s) seen[s] = sor[1][s];
-        __syncthreads();
-        const unsigned int um = unfinished<P>(seen, all, active);
-        uint64_t acc[P];
-#pragma unroll
-        for (int s = 0; s < P; ++s) acc[s] = 0;
-        if (um) {  // uniform: seen comes from shared memory
-            for (int64_t b0 = a0; b0 < a1; b0 += Gath<P>::G * kThreads) {
-                gather<P>(nwc, fb, w.adj, b0 + threadIdx.x, kThreads, a1, acc);
-#pragma unroll
-                for (int s = 0; s < P; ++s) {
-                    const uint64_t wa = warp_or(acc[s]);
-                    if ((threadIdx.x & 31) == 0) sor[threadIdx.x >> 5][s] = wa;
-                }
-                __syncthreads();
-                if (threadIdx.x < P) {
-                    uint64_t x = 0;
-                    for (int k = 0; k < kWarps; ++k) x |= sor[k][threadIdx.x];
-                    sor[0][threadIdx.x] = x;
-                }
-                __syncthreads();
-#pragma unroll
-                for (int s = 0; s < P; ++s) acc[s] = sor[0][s];
-                __syncthreads();
-                if (missing_bits<P>(acc, seen, all, um) == 0) break;
-            }
-        }
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int s = 0; s < P; ++s) {
-                const uint64_t nb_ = acc[s] & ~seen[s];
-                if (nb_) atomicOr(reinterpret_cast<unsigned long long*>(w.acc + (size_t)v * P + s), (unsigned long long)nb_);
-            }
-            __threadfence();  // this piece's ORs before its count
-            const unsigned int npc = (unsigned int)((o1 - o0 + kBigDeg - 1) / kBigDeg);
-            if (atomicAdd(w.piece_cnt + v, 1u) == npc - 1) {
-                // every piece of v has ORed its part: v's vertex phase of round + 1
-                __threadfence();
-                w.piece_cnt[v] = 0u;
-                uint64_t vs[P], ac[P];
-                load_words<P>(w.vis + (size_t)v * P, vs);
-#pragma unroll
-                for (int s = 0; s < P; ++s) ac[s] = __ldcg(reinterpret_cast<const unsigned long long*>(w.acc + (size_t)v * P + s));
-                zero_words<P>(w.acc + (size_t)v * P);
-                if (pull_finish<P>(w, v, ac, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act))
-                    atomicOr(fbn + (v >> 5), 1u << (v & 31));
-            }
-        }
-    }
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int64_t nw_total = ((int64_t)gridDim.x * kThreads) >> 5;
-    // warp per mid-degree vertex
-    for (int64_t i = gw; i < nm; i += nw_total) {
-        const int32_t v = (int32_t)(nb + i);
-        uint64_t vs[P];
-        load_words<P>(w.vis + (size_t)v * P, vs);
-        const unsigned int um = unfinished<P>(vs, all, active);
-        if (!um) continue;
-        const int64_t o0 = w.off[v], o1 = w.off[v + 1];
-        uint64_t acc[P];
-#pragma unroll
-        for (int s = 0; s < P; ++s) acc[s] = 0;
-        for (int64_t b0 = o0; b0 < o1; b0 += 32 * Gath<P>::G) {
-            gather<P>(nwc, fb, w.adj, b0 + lane, 32, o1, acc);
-#pragma unroll
-            for (int s = 0; s < P; ++s) acc[s] = warp_or(acc[s]);
-            if (missing_bits<P>(acc, vs, all, um) == 0) break;
-        }
-        if (lane == 0 && pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act))
-            atomicOr(fbn + (v >> 5), 1u << (v & 31));
-    }
-    // low-degree vertices: a warp takes 32 consecutive ones, whose lists are
-    // consecutive in the internal order, stages them in shared memory with
-    // coalesced loads, then each lane scans its own list
-    int32_t* wadj = sadj[wib];
-    const int64_t small0 = nb + nm;
-    for (int64_t g0 = gw * 32; g0 < ns; g0 += nw_total * 32) {
-        const int64_t i = g0 + lane;
-        const bool has = i < ns;
-        const int32_t v = has ? (int32_t)(small0 + i) : 0;
-        const int64_t o0 = has ? w.off[v] : 0, o1 = has ? w.off[v + 1] : 0;
-        const int last = (int)((ns - 1 - g0) < 31 ? (ns - 1 - g0) : 31);
-        const int64_t lo = __shfl_sync(0xffffffffu, o0, 0);
-        const int64_t hi = __shfl_sync(0xffffffffu, o1, last);
-        for (int64_t x = lo + lane; x < hi; x += 32) wadj[x - lo] = w.adj[x];
-        __syncwarp();
-        bool joined = false;
-        if (has) {
-            uint64_t vs[P];
-            load_words<P>(w.vis + (size_t)v * P, vs);
-            const unsigned int um = unfinished<P>(vs, all, active);
-            if (um) {
-                uint64_t acc[P];
-#pragma unroll
-                for (int s = 0; s < P; ++s) acc[s] = 0;
-                for (int64_t e = o0; e < o1; e += Gath<P>::G) {
-                    gather<P>(nwc, fb, wadj - lo, e, 1, o1, acc);
-                    if (missing_bits<P>(acc, vs, all, um) == 0) break;
-                }
-                joined = pull_finish<P>(w, v, acc, vs, (uint32_t)(o1 - o0), rn, nwn, my_cnt, my_sdeg, my_act);
-            }
-        }
-        // the 32 vertices are consecutive: their bits span at most two bitmap words
-        const unsigned int jm = __ballot_sync(0xffffffffu, joined);
-        if (lane == 0 && jm) {
-            const int32_t v0 = (int32_t)(small0 + g0);
-            const int sh = v0 & 31;
-            atomicOr(fbn + (v0 >> 5), jm << sh);
-            if (sh && (jm >> (32 - sh))) atomicOr(fbn + (v0 >> 5) + 1, jm >> (32 - sh));
-        }
-        __syncwarp();
-    }
-    // publish the next frontier's size, arcs and active slots: one atomic each per CTA
-    __shared__ unsigned long long red[kWarps];
-    __shared__ unsigned int s_act;
-    if (threadIdx.x == 0) s_act = 0;
-    const unsigned long long bc = block_sum(my_cnt, red);
-    const unsigned long long bs = block_sum(my_sdeg, red);
-    const unsigned int wact = __reduce_or_sync(0xffffffffu, my_act);
-    if (lane == 0 && wact) atomicOr(&s_act, wact);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (bc) {
-            atomicAdd(&cn->qlen, bc);
-            atomicAdd(&cn->nf, bc);
-        }
-        if (bs) atomicAdd(&cn->sdeg, bs);
-        if (s_act) atomicOr(&cn->slot_active, s_act);
-        if (blockIdx.x == 0) cn->dense = 1;
-    }
+    pull_round<P, FUSE>(w, c, cn, round, qlen, fb, fbn, stamp, sall, &s_work, sor, sadj);
 }
 
 // Writes the wave's internal rows to the caller's outputs: caller vertex v
@@ -880,7 +929,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             if (s >= w.nslots) continue;
-            const uint32_t wm = ((reached >> s) & 1u) && d ? wr[s] : 0u;
+            const uint32_t wm = !((reached >> s) & 1u) || !d ? 0u : d > kZeroWords ? wr[s] : 0xFFFFu;
             for (int j = 0; j < d; ++j)
                 ss[s].masks[(size_t)j * (size_t)w.n + v] = ((wm >> j) & 1u) ? mr[(size_t)s * d + j] : 0ull;
         }
@@ -891,10 +940,14 @@ template __global__ void k_phase_a<1>(Wave, int);
 template __global__ void k_phase_a<2>(Wave, int);
 template __global__ void k_phase_a<4>(Wave, int);
 template __global__ void k_phase_a<8>(Wave, int);
-template __global__ void k_phase_b<1>(Wave, int);
-template __global__ void k_phase_b<2>(Wave, int);
-template __global__ void k_phase_b<4>(Wave, int);
-template __global__ void k_phase_b<8>(Wave, int);
+template __global__ void k_phase_b<1, false>(Wave, int);
+template __global__ void k_phase_b<2, false>(Wave, int);
+template __global__ void k_phase_b<4, false>(Wave, int);
+template __global__ void k_phase_b<8, false>(Wave, int);
+template __global__ void k_phase_b<1, true>(Wave, int);
+template __global__ void k_phase_b<2, true>(Wave, int);
+template __global__ void k_phase_b<4, true>(Wave, int);
+template __global__ void k_phase_b<8, true>(Wave, int);
 template __global__ void k_emit<1>(Wave, const int32_t*);
 template __global__ void k_emit<2>(Wave, const int32_t*);
 template __global__ void k_emit<4>(Wave, const int32_t*);
@@ -905,7 +958,8 @@ cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, in
 #define CBFS_CASE(PP)                                                       \
     case PP:                                                                \
         if (which == 0) k_phase_a<PP><<<grid, kThreads, 0, st>>>(w, round); \
-        else if (which == 1) k_phase_b<PP><<<grid, kThreads, 0, st>>>(w, round); \
+        else if (which == 1 && w.fused_pull) k_phase_b<PP, true><<<grid, kThreads, 0, st>>>(w, round); \
+        else if (which == 1) k_phase_b<PP, false><<<grid, kThreads, 0, st>>>(w, round); \
         else k_emit<PP><<<grid, kThreads, 0, st>>>(w, iperm);               \
         break;
         CBFS_CASE(1)
@@ -1324,7 +1378,8 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         const int cnt = (int)(seed_off[wv + 1] - seed_off[wv]);
         e = cudaMemsetAsync(w.vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.nw0, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, cs);
+        if (e == cudaSuccess && w.fused_pull)  // a fused pull round may read any vertex's entry
+            e = cudaMemsetAsync(w.nw0, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.rq, 0, sizeof(uint32_t) * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.fb0, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.dist_r, 0xFF, (size_t)P * (size_t)n, cs);
@@ -1751,7 +1806,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.wmask_r = g->wmask_r;
     w.masks_r = g->masks_r;
     w.dense_div = dense_div;
-    w.rows_in_pull = (tune && tune->rows_in_pull > 0) ? 1 : 0;
+    w.fused_pull = (tune && tune->fused_pull > 0) ? 1 : 0;
 
     // Graph mode (device outputs): the call runs as one cached CUDA graph per
     // call shape whose rounds loop on the device, and is stream-ordered: the
@@ -1830,7 +1885,8 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         w.slots = g->slots + (size_t)wv * P;
         CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
-        CK(cudaMemsetAsync(g->nw, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, st));
+        if (w.fused_pull)  // a fused pull round may read any vertex's entry
+            CK(cudaMemsetAsync(g->nw, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->rq, 0, sizeof(uint32_t) * (size_t)n, st));
         CK(cudaMemsetAsync(g->fb, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, st));
         CK(cudaMemsetAsync(g->dist_r, 0xFF, (size_t)P * (size_t)n, st));
@@ -2031,8 +2087,8 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     g->n_mid = (int64_t)hs.n_mid;
     g->n_big = (int64_t)hs.n_big;
     g->big_pieces = (int64_t)hs.big_pieces;
-    const void* kb[4] = {(const void*)k_phase_b<1>, (const void*)k_phase_b<2>, (const void*)k_phase_b<4>,
-                         (const void*)k_phase_b<8>};
+    const void* kb[4] = {(const void*)k_phase_b<1, false>, (const void*)k_phase_b<2, false>,
+                         (const void*)k_phase_b<4, false>, (const void*)k_phase_b<8, false>};
     for (int i = 0; i < 4; ++i) {
         // the default carveout: a larger shared-memory share would shrink the L1 these
         // gather-bound kernels depend on (measured slower)

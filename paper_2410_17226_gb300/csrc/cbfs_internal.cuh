@@ -22,6 +22,9 @@ constexpr int64_t kPullMid = 2048;  // pull: warp per vertex up to this degree, 
 constexpr int kMaxMidDeg = 65536;   // largest warp-per-vertex threshold a call may ask for
 constexpr int kDefaultMidDeg = 16384;  // a call's default: warps beat 2048-arc CTA pieces up to
                                        // about this degree on power-law graphs (measured)
+constexpr int kZeroWords = 4;       // a slot's subset words are zeroed at its first visit up to
+                                    // this d (one 32-byte sector); above it a mask records the
+                                    // words written
 constexpr int kTileMin = kThreads;  // smallest phase-A tile (P >= 4)
 constexpr int kTileMax = 4 * kThreads;
 
@@ -54,7 +57,7 @@ struct RoundCtl {
     int mode;                  // 0 push, 1 pull: decided by phase A from qlen and sdeg
     int dense;                 // 1: F_i was produced by a pull round and is not in the queue;
                                //    phase A finds it by scanning every vertex's acc block
-    unsigned int pad;
+    int fused;                 // 1: that pull did F_i's vertex phase (new sources in nw[i & 1])
 };
 
 // A frontier vertex whose list is longer than kBigDeg (push mode).
@@ -115,8 +118,8 @@ struct Wave {
     uint16_t* wmask_r;      // [n][P] bit j: masks_r word j of the slot was written in this
                             // wave (started at the slot's first visit; never cleared)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
-    int rows_in_pull;       // 1: a pull records the rows of the vertices it finishes; 0: the
-                            //    next vertex phase does
+    int fused_pull;         // 1: pull rounds do their vertices' vertex phase on the spot
+                            //    (vis, rows, nw; nw cleared per wave); 0: plain pulls
     int* round_dev;         // graph mode: the current round lives here (nullptr: kernel argument)
     unsigned long long* iters;  // graph mode: rounds executed (for the launch accounting)
     int* status;
@@ -144,7 +147,7 @@ __global__ void k_seed(Wave w, const uint64_t* seeds, int count);
 __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count, int bound_round, int* unfinished);
 template <int P>
 __global__ void k_phase_a(Wave w, int round);
-template <int P>
+template <int P, bool FUSE>  // FUSE: the call's fused_pull
 __global__ void k_phase_b(Wave w, int round);
 // Writes the wave's internal rows to the caller's cluster-major outputs.
 template <int P>

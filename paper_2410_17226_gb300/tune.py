@@ -54,7 +54,7 @@ def autotune(g: "cbfs.Graph", clusters, d: int, sample: int = 32, alphas=ALPHAS,
              small_degs=SMALL_DEGS, mid_degs=MID_DEGS, key_extra: str = "", use_cache: bool = True,
              write_cache: bool = True, stream=None) -> dict:
     """Returns ``{"pull_alpha": a, "slots": s, "small_deg": t, "mid_deg": m,
-    "rows_in_pull": r, "ms": best, "table": {...}}``."""
+    "fused_pull": r, "ms": best, "table": {...}}``."""
     key = graph_key(g, d, key_extra)
     if use_cache:
         hit = _load().get(key)
@@ -91,13 +91,13 @@ def autotune(g: "cbfs.Graph", clusters, d: int, sample: int = 32, alphas=ALPHAS,
             table[f"a={best['pull_alpha']},s={best['slots']},t={t},m={m}"] = round(ms, 3)
             if ms < best["ms"]:
                 best = dict(tune, ms=ms)
-    # where a pull round writes the rows of the vertices it finishes (the pull
-    # itself, or the next vertex phase): graphs differ
+    # plain or fused pull rounds (the vertex phase of the next round done by
+    # the pull): graphs differ
     tune = {k: best[k] for k in ("pull_alpha", "slots", "small_deg", "mid_deg")}
-    tune["rows_in_pull"] = 1
+    tune["fused_pull"] = 1
     ms = timed(tune)
-    table[f"a={best['pull_alpha']},s={best['slots']},t={best['small_deg']},m={best['mid_deg']},rows_in_pull"] = round(ms, 3)
-    best["rows_in_pull"] = 0
+    table[f"a={best['pull_alpha']},s={best['slots']},t={best['small_deg']},m={best['mid_deg']},fused_pull"] = round(ms, 3)
+    best["fused_pull"] = 0
     if ms < best["ms"]:
         best = dict(tune, ms=ms)
     best["table"] = table

@@ -66,7 +66,7 @@ def test_config2_scale22_256_clusters_batched(cb):
     g = cb.Graph(off, adj)
     tn = tune.autotune(g, clusters, d, key_extra=f"rmat-s22-{tune.signature(off)}")
     tset = {"pull_alpha": tn["pull_alpha"], "slots": tn["slots"], "small_deg": tn.get("small_deg", 0),
-            "mid_deg": tn.get("mid_deg", 0), "rows_in_pull": tn.get("rows_in_pull", 0)}
+            "mid_deg": tn.get("mid_deg", 0), "fused_pull": tn.get("fused_pull", 0)}
     dist, masks = g.run_batched(clusters, d, tune=tset)
     assert_invariants(dist, masks, clusters)
     assert assert_equal_oracle(off, adj, clusters, d, dist, masks, range(256)) == 256

@@ -99,7 +99,7 @@ def test_batched_equals_single_and_oracle(cb):
     for tune in (None, {"slots": 1}, {"slots": 3}, {"slots": 16}, dict(PUSH_ONLY, slots=4),
                  dict(PULL_EAGER, slots=5), {"slots": 8, "host_loop": 1}, {"slots": 2, "dense_div": -1},
                  {"slots": 4, "dense_div": 1}, dict(PUSH_ONLY, slots=8, host_loop=1),
-                 dict(PULL_EAGER, slots=4, rows_in_pull=1), {"slots": 8, "rows_in_pull": 1, "host_loop": 1}):
+                 dict(PULL_EAGER, slots=4, fused_pull=1), {"slots": 8, "fused_pull": 1, "host_loop": 1}):
         # the first call of a shape runs host-driven, a repeat replays a CUDA graph
         for rep in range(2):
             bd, bm = g.run_batched(clusters, d, tune=tune)
@@ -299,7 +299,7 @@ def test_pull_degree_classes_equal_oracle(cb, small, mid):
                          {"slots": slots, "pull_alpha": 1e-9, "small_deg": small, "mid_deg": mid,
                           "sparse_mid_deg": max(small, 40)},  # other classes in sparse rounds
                          {"slots": slots, "pull_alpha": 1e-9, "small_deg": small, "mid_deg": mid,
-                          "rows_in_pull": 1},  # hub pieces finish their vertex with its rows
+                          "fused_pull": 1},  # the last hub piece does the hub's vertex phase
                          {"slots": slots, "pull_alpha": 1e-9}):  # back to the defaults
                 for _ in range(2):
                     dist, masks = g.run_batched(clusters, d, tune=tune)
@@ -342,20 +342,20 @@ def test_empty_graph_and_empty_calls(cb):
     assert int(d2.min()) == 7 and int(m2.min()) == 7  # untouched
 
 
-@pytest.mark.parametrize("slots,rows_in_pull", [(1, 0), (4, 0), (4, 1)])
-def test_largest_diameter_bound(cb, slots, rows_in_pull):
+@pytest.mark.parametrize("slots,fused_pull", [(1, 0), (4, 0), (4, 1)])
+def test_largest_diameter_bound(cb, slots, fused_pull):
     """d = 15, the largest bound: sources 15 apart on a path and a grid
     ball of diameter up to 15; every offset 0..15 occurs."""
     off, adj = I.path(60)
     g = cb.Graph(off, adj)
     clusters = [np.array([10, 25], np.int32), np.array([0, 5, 15], np.int32), np.array([40, 55, 47], np.int32)]
-    dist, masks = g.run_batched(clusters, 15, tune={"slots": slots, "rows_in_pull": rows_in_pull})
+    dist, masks = g.run_batched(clusters, 15, tune={"slots": slots, "fused_pull": fused_pull})
     for c, S in enumerate(clusters):
         od, om = O.cbfs_alg1(off, adj, S, 15)
         assert (dist[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(masks[c]) == om).all()
     goff, gadj = I.grid(20, 20)
     gg = cb.Graph(goff, gadj)
     S = np.array([0, 7, 8 * 20], np.int32)  # (0,0), (7,0), (0,8): 7, 8 and 15 apart
-    gd, gm = gg.run_batched([S], 15, tune={"slots": slots, "rows_in_pull": rows_in_pull})
+    gd, gm = gg.run_batched([S], 15, tune={"slots": slots, "fused_pull": fused_pull})
     od, om = O.cbfs_alg1(goff, gadj, S, 15)
     assert (gd[0].cpu().numpy() == od).all() and (cb.as_numpy_u64(gm[0]) == om).all()
