@@ -78,21 +78,29 @@ def test_config2_scale22_256_clusters_batched(cb):
 def test_config3_road_grid_4096_ball_clusters(cb):
     """4096 x 4096 grid, 10 % of edges deleted, 1 % shortcuts, 64 clusters of
     64 sources (BFS balls, d = their largest exact diameter), in launches of
-    16 clusters (the benchmark's) to bound the d-word outputs: all 64 clusters
-    equal the oracle."""
+    16 clusters with the benchmark's autotuned settings: all 64 clusters equal
+    the oracle; two of them also with the other pull variant."""
+    from paper_2410_17226_gb300 import tune
+
     off, adj = I.road_grid(4096)
     clusters, ds = I.ball_clusters(off, adj, 64, 64, seed=I.MASTER_SEED + 3)
     d = max(ds)
     g = cb.Graph(off, adj)
+    # the benchmark's autotuned settings (the fused pull on this graph)
+    tn = tune.autotune(g, clusters, d, sample=16, key_extra=f"grid-4096-{tune.signature(off)}")
+    tset = {k: tn.get(k, 0) for k in ("pull_alpha", "slots", "small_deg", "mid_deg", "fused_pull")}
     checked = 0
     for b in range(0, 64, 16):
         part = clusters[b:b + 16]
-        dist, masks = g.run_batched(part, d)
+        dist, masks = g.run_batched(part, d, tune=tset)
         assert_invariants(dist, masks, part)
         # at d = 12 one cluster's outputs are 1.6 GB: at most 16 on the host at once
         checked += assert_equal_oracle(off, adj, part, d, dist, masks, range(len(part)), workers=min(16, host_cores()))
         del dist, masks
     assert checked == 64
+    other = dict(tset, fused_pull=0 if tset.get("fused_pull") else 1)
+    dist, masks = g.run_batched(clusters[:2], d, tune=other)
+    assert assert_equal_oracle(off, adj, clusters[:2], d, dist, masks, range(2)) == 2
 
 
 def test_config4_scale24_1024_degree_clusters_labels(cb):
