@@ -31,6 +31,7 @@ def main(argv=None) -> int:
     ap.add_argument("--small-deg", type=int, default=0, help="thread-per-vertex degree limit (0: default)")
     ap.add_argument("--mid-deg", type=int, default=0, help="warp-per-vertex degree limit (0: default)")
     ap.add_argument("--host-loop", action="store_true", help="host-driven rounds instead of a CUDA graph")
+    ap.add_argument("--fused-pull", action="store_true", help="pull rounds do the next vertex phase (tune.fused_pull)")
     ap.add_argument("--repeat", type=int, default=0, help="extra calls after the first")
     args = ap.parse_args(argv)
 
@@ -46,7 +47,7 @@ def main(argv=None) -> int:
     dist = torch.empty((C, g.n), dtype=torch.uint8, device="cuda")
     masks = torch.empty((C, d, g.n), dtype=torch.int64, device="cuda")
     tune = {"slots": args.slots, "pull_alpha": args.pull_alpha, "host_loop": int(args.host_loop),
-            "small_deg": args.small_deg, "mid_deg": args.mid_deg}
+            "small_deg": args.small_deg, "mid_deg": args.mid_deg, "fused_pull": int(args.fused_pull)}
     ms = 0.0
     for _ in range(1 + args.repeat):
         torch.cuda.synchronize()
