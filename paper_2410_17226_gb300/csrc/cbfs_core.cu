@@ -957,7 +957,7 @@ cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, in
     switch (w.P) {
 #define CBFS_CASE(PP)                                                       \
     case PP:                                                                \
-        if (which == 0) k_phase_a<PP><<<grid, kThreads, 0, st>>>(w, round); \
+        if (which == 0) k_phase_a<PP><<<w.grid_a > 0 ? w.grid_a : grid, kThreads, 0, st>>>(w, round); \
         else if (which == 1 && w.fused_pull) k_phase_b<PP, true><<<grid, kThreads, 0, st>>>(w, round); \
         else if (which == 1) k_phase_b<PP, false><<<grid, kThreads, 0, st>>>(w, round); \
         else k_emit<PP><<<grid, kThreads, 0, st>>>(w, iperm);               \
@@ -1104,7 +1104,8 @@ struct cbfs_graph_s {
         int64_t count;
     };
     std::vector<HubPieces> pieces;
-    int grid_p[4] = {0, 0, 0, 0};  // phase-kernel grid for P = 1, 2, 4, 8 (SMs x resident CTAs)
+    int grid_p[4] = {0, 0, 0, 0};  // edge-phase grid for P = 1, 2, 4, 8 (SMs x resident CTAs)
+    int grid_a[4] = {0, 0, 0, 0};  // vertex-phase grid (latency-bound: as many CTAs as fit)
     int device = 0;
     // scratch, sized for cap_slots clusters in flight
     int cap_slots = 0;
@@ -1645,7 +1646,8 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     rc = ensure_scratch(g, P);
     if (!rc) rc = ensure_dev(&g->masks_r, &g->masks_r_cap, std::max<int64_t>(1, g->n * d * P));
     if (rc) return rc;
-    const int grid = g->grid_p[P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3];
+    const int pi = P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3;
+    const int grid = g->grid_p[pi];
     const int nwaves = (C + P - 1) / P;
     const int64_t total_src = coff[C];
     const int64_t n = g->n;
@@ -1806,6 +1808,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.wmask_r = g->wmask_r;
     w.masks_r = g->masks_r;
     w.dense_div = dense_div;
+    w.grid_a = g->grid_a[pi];
     w.fused_pull = (tune && tune->fused_pull > 0) ? 1 : 0;
 
     // Graph mode (device outputs): the call runs as one cached CUDA graph per
@@ -2089,12 +2092,17 @@ int cbfs_graph_create(int64_t n, const void* off, int off_is_i64, const int32_t*
     g->big_pieces = (int64_t)hs.big_pieces;
     const void* kb[4] = {(const void*)k_phase_b<1, false>, (const void*)k_phase_b<2, false>,
                          (const void*)k_phase_b<4, false>, (const void*)k_phase_b<8, false>};
+    const void* ka[4] = {(const void*)k_phase_a<1>, (const void*)k_phase_a<2>, (const void*)k_phase_a<4>,
+                         (const void*)k_phase_a<8>};
     for (int i = 0; i < 4; ++i) {
         // the default carveout: a larger shared-memory share would shrink the L1 these
         // gather-bound kernels depend on (measured slower)
         occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb[i], kThreads, 0);
         g->grid_p[i] = sms * std::max(1, std::min(occ, 8));
+        occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka[i], kThreads, 0);
+        g->grid_a[i] = sms * std::max(1, std::min(occ, 8));
     }
     // internal order: ranks by degree (cbfs_relabel.cu); the degree classes are rank ranges
     e = rank_order_device(n, g->off, hs.maxdeg, scratch, g->perm, g->iperm_d, g->off_r, d_stats, sms, st);

@@ -118,6 +118,7 @@ struct Wave {
     uint16_t* wmask_r;      // [n][P] bit j: masks_r word j of the slot was written in this
                             // wave (started at the slot's first visit; never cleared)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
+    int grid_a;             // CTAs of the vertex phase (0: the edge phase's grid)
     int fused_pull;         // 1: pull rounds do their vertices' vertex phase on the spot
                             //    (vis, rows, nw; nw cleared per wave); 0: plain pulls
     int* round_dev;         // graph mode: the current round lives here (nullptr: kernel argument)
