@@ -282,10 +282,14 @@ __device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], cons
     return um;
 }
 
-// Records the sources fw new at u in round `round` in u's rows (Algorithm 1's
-// S_u[round - Delta_u] = Snew, Delta_u = round on the first visit of a slot):
-// the wave's internal rows (dist_r path) or the caller's arrays directly (one
-// slot in the caller's ids, ss[0]).  Returns the slots with new sources.
+// Records the sources fw new at u in round `round` (Algorithm 1's
+// S_u[round - Delta_u] = Snew, Delta_u = round on the first visit of a slot)
+// either in the wave's internal rows (dist_r path, emitted to the caller's
+// arrays after the wave) or, when the wave has no rows (dist_r == nullptr),
+// straight into each slot's cluster-major output at the caller's id
+// perm[u] (identity when perm is null); those outputs were cleared to
+// Delta = 0xFF and empty subsets before the wave.  Returns the slots with
+// new sources.
 template <int P>
 __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, const uint64_t (&fw)[P], int round,
                                                     const SlotDesc* ss) {
@@ -327,20 +331,25 @@ __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, c
             act |= 1u << s;
         }
     } else {
-        // direct: one cluster, caller's ids, caller's arrays
-        const SlotDesc& S = ss[0];
-        const uint8_t dd = S.dist[u];
-        int j;
-        if (dd == 0xFF) {
-            if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
-            else S.dist[u] = (uint8_t)round;
-            j = 0;
-        } else {
-            j = round - (int)dd;
+        // direct: each slot's cluster-major output at the caller's id
+        const size_t id = w.perm ? (size_t)w.perm[u] : (size_t)u;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            if (!fw[s]) continue;
+            const SlotDesc& S = ss[s];
+            const uint8_t dd = S.dist[id];
+            int j;
+            if (dd == 0xFF) {
+                if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
+                else S.dist[id] = (uint8_t)round;
+                j = 0;
+            } else {
+                j = round - (int)dd;
+            }
+            if (j < w.d) S.masks[(size_t)j * (size_t)w.n + id] = fw[s];
+            else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
+            act |= 1u << s;
         }
-        if (j < w.d) S.masks[(size_t)j * (size_t)w.n + u] = fw[0];
-        else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
-        act = 1u;
     }
     return act;
 }
@@ -424,6 +433,18 @@ __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count, int bo
         const uint32_t v = (uint32_t)e;
         if ((int64_t)v >= w.n || s >= w.P) continue;  // flagged by k_seed
         if (w.vis[(size_t)v * w.P + s] != w.slots[s].all) set_status(w.status, CBFS_E_DIAMETER);
+    }
+}
+
+// A wave without internal rows writes its slots' outputs directly: before
+// it, every slot's dist is set to 0xFF and its d subset words to 0.
+__global__ void k_clear_outputs(Wave w) {
+    const int64_t n = w.n, words = (int64_t)w.d * n;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, step = (int64_t)gridDim.x * blockDim.x;
+    for (int s = 0; s < w.nslots; ++s) {
+        const SlotDesc S = w.slots[s];
+        for (int64_t i = t0; i < n; i += step) S.dist[i] = 0xFF;
+        for (int64_t i = t0; i < words; i += step) S.masks[i] = 0ull;
     }
 }
 
@@ -1383,10 +1404,11 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
             e = cudaMemsetAsync(w.nw0, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.rq, 0, sizeof(uint32_t) * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.fb0, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, cs);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.dist_r, 0xFF, (size_t)P * (size_t)n, cs);
+        if (e == cudaSuccess && w.dist_r) e = cudaMemsetAsync(w.dist_r, 0xFF, (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, sizeof(RoundCtl) * kMaxRounds, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.round_dev, 0, sizeof(int), cs);
         if (e != cudaSuccess) break;
+        if (!w.dist_r) k_clear_outputs<<<grid, kThreads, 0, cs>>>(w);
         k_seed<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         // the round loop: a conditional WHILE node spliced into the capture
@@ -1420,7 +1442,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         e = cudaStreamEndCapture(cs2, &body_out);
         if (e == cudaSuccess) e = eb;
         if (e != cudaSuccess) break;
-        if ((e = launch_round(w, 0, grid, cs, 2, g->iperm_d)) != cudaSuccess) break;
+        if (w.dist_r && (e = launch_round(w, 0, grid, cs, 2, g->iperm_d)) != cudaSuccess) break;
         k_check_sources<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt, 0, nullptr);
         e = cudaGetLastError();
     }
@@ -1810,6 +1832,13 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.dense_div = dense_div;
     w.grid_a = g->grid_a[pi];
     w.fused_pull = (tune && tune->fused_pull > 0) ? 1 : 0;
+    if (w.fused_pull) {
+        // no internal rows: the vertex phase (in the pull or in phase A) writes the
+        // slots' outputs directly, cleared per wave (k_clear_outputs); no emit
+        w.dist_r = nullptr;
+        w.masks_r = nullptr;
+        w.wmask_r = nullptr;
+    }
 
     // Graph mode (device outputs): the call runs as one cached CUDA graph per
     // call shape whose rounds loop on the device, and is stream-ordered: the
@@ -1892,10 +1921,14 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
             CK(cudaMemsetAsync(g->nw, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->rq, 0, sizeof(uint32_t) * (size_t)n, st));
         CK(cudaMemsetAsync(g->fb, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, st));
-        CK(cudaMemsetAsync(g->dist_r, 0xFF, (size_t)P * (size_t)n, st));
+        if (w.dist_r) CK(cudaMemsetAsync(g->dist_r, 0xFF, (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->ctl, 0, sizeof(RoundCtl) * kMaxRounds, st));
         const int cnt = (int)(wave_seed_off[wv + 1] - wave_seed_off[wv]);
+        // direct outputs are written from the wave's start: its ring slot must have
+        // been copied out first (wave wv - G)
+        if (!w.dist_r && host_out) CK(cudaStreamWaitEvent(st, g->ev_copy[wv % G], 0));
         int ev = prof_begin(g, 0, st);
+        if (!w.dist_r) k_clear_outputs<<<grid, kThreads, 0, st>>>(w);
         k_seed<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
         prof_end(g, ev, st);
         CK(cudaGetLastError());
@@ -1934,10 +1967,12 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
             }
         }
         const int b = wv % G;
-        if (host_out) CK(cudaStreamWaitEvent(st, g->ev_copy[b], 0));  // ring slot b copied out (wave wv - G)
-        ev = prof_begin(g, 0, st);
-        CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
-        prof_end(g, ev, st);
+        if (host_out && w.dist_r) CK(cudaStreamWaitEvent(st, g->ev_copy[b], 0));  // ring slot b copied out (wave wv - G)
+        if (w.dist_r) {
+            ev = prof_begin(g, 0, st);
+            CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
+            prof_end(g, ev, st);
+        }
         if (host_out && (rerun || (wv + 1) % CG == 0 || wv == nwaves - 1)) {
             // the group's waves sit in consecutive ring slots (G is a multiple of CG)
             const int g0 = rerun ? wv : wv / CG * CG;

@@ -114,7 +114,8 @@ struct Wave {
     const int32_t* perm;    // internal vertex -> caller's id for the outputs (nullptr: identity)
     uint8_t* dist_r;        // [n][P] Delta rows of the wave in internal order, emitted to the
     uint64_t* masks_r;      // [n][P][d] caller's arrays after the wave; nullptr: the vertex
-                            // phase writes the caller's arrays directly (P = 1, no perm)
+                            // phase writes each slot's output directly at perm[u] (waves with
+                            // fused pulls, and the allocation-free entry point)
     uint16_t* wmask_r;      // [n][P] bit j: masks_r word j of the slot was written in this
                             // wave (started at the slot's first visit; never cleared)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
