@@ -729,6 +729,7 @@ def run_cbfs(args, ws, rank, local):
 
     st = g.output_stats(dist, masks, ks, d)
     V, A, R = int(st[:, 0].sum()), int(st[:, 1].sum()), st[:, 2]
+    lockstep = lockstep_rounds(ks, st[:, 3], tset["slots"])
     src_edges = int(sum(int(k) * int(r) // 2 for k, r in zip(ks, R)))
     value = job_value(src_edges * args.steps, ws, t_max)
     alg_bytes_step = ARC_BYTES * A + VERTEX_BYTES * V + C * n * (1 + 8 * d)
@@ -960,6 +961,7 @@ def run_cbfs(args, ws, rank, local):
                                   "labels_query": round((t_ms - cbfs_ms) / args.steps, 3)},
             "alg_gbs_step": round(alg_bytes_step * args.steps / (t_ms / 1e3) / 1e9, 1),
             "work_per_step": {"V": V, "A": A, "source_edges": src_edges, "alg_bytes": int(alg_bytes_step)},
+            "lockstep": lockstep,
             "kernel_ms_one_untimed_step": {k: split[k] for k in ("setup", "vertex_phase", "edge_phase")},
             "query": query,
             "serving": serving,
@@ -973,6 +975,23 @@ def run_cbfs(args, ws, rank, local):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def lockstep_rounds(ks, rounds, slots: int) -> dict:
+    """How long clusters wait for each other in the lockstep waves: the
+    library groups a call's clusters into waves of `slots` by size (sizes
+    descending, ties in call order), and a wave runs as many rounds as its
+    deepest cluster.  Returns the rounds the waves ran against the rounds
+    their clusters needed (slot-rounds), so 1 - ratio is the idle share."""
+    ks = np.asarray(ks)
+    rounds = np.asarray(rounds, dtype=np.int64)
+    order = np.argsort(-ks, kind="stable")
+    P = max(1, int(slots))
+    wave_rounds = [int(rounds[order[i:i + P]].max()) for i in range(0, len(order), P)]
+    used = int(rounds.sum())
+    offered = sum(r * min(P, len(order) - i * P) for i, r in enumerate(wave_rounds))
+    return {"waves": len(wave_rounds), "wave_rounds": int(sum(wave_rounds)), "cluster_rounds": used,
+            "busy_slot_round_share": round(used / max(offered, 1), 4)}
 
 
 def summary_of(line: dict) -> dict:

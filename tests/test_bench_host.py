@@ -70,3 +70,13 @@ def test_summary_of_a_line_keeps_every_workload():
     assert s2["serving_0.5x_p50_p99_ms"] == [None, None] and "road_grid_4096" not in s2
     import json
     assert len(json.dumps(s)) < 1200
+
+
+def test_lockstep_rounds_counts_idle_slot_rounds():
+    # sizes 5, 3, 9, 1 in waves of 2 by size: (9, 5) and (3, 1)
+    ks = [5, 3, 9, 1]
+    rounds = [4, 6, 8, 2]
+    out = bench.lockstep_rounds(ks, rounds, 2)
+    assert out["waves"] == 2 and out["wave_rounds"] == 8 + 6
+    assert out["cluster_rounds"] == 20
+    assert out["busy_slot_round_share"] == round(20 / (2 * 8 + 2 * 6), 4)
