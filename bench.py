@@ -464,6 +464,7 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
         dist = torch.empty((per_launch, n), dtype=torch.uint8, device="cuda")
         masks = torch.empty((per_launch, d, n), dtype=torch.int64, device="cuda")
         total_ms, A, V, src_edges, rounds = 0.0, 0, 0, 0, 0
+        lock = {"waves": 0, "wave_rounds": 0, "cluster_rounds": 0}
         for b in range(0, count, per_launch):
             part = clusters[b:b + per_launch]
             k = len(part)
@@ -473,6 +474,9 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
             A += int(st[:, 1].sum())
             V += int(st[:, 0].sum())
             rounds = max(rounds, int(st[:, 3].max()))
+            ls = lockstep_rounds([len(S) for S in part], st[:, 3], tset["slots"])
+            for key in lock:
+                lock[key] += ls[key]
             reached = dist[:k].cpu().numpy() != 255
             for c, S in enumerate(part):
                 src_edges += len(S) * int(deg[reached[c]].sum()) // 2
@@ -484,6 +488,8 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
             "clusters": count, "d": d, "per_launch": per_launch, "tune": dict(tset, cached=tn.get("cached")),
             "ms_all_clusters": round(total_ms, 2),
             "gteps": round(src_edges / (total_ms / 1e3) / 1e9, 2), "max_rounds": rounds,
+            "lockstep": dict(lock, busy_slot_round_share=round(
+                lock["cluster_rounds"] / max(lock["wave_rounds"] * max(int(tset["slots"]), 1), 1), 4)),
             "arcs_per_s": round(A / (total_ms / 1e3), 1),
             "alg_gbs": round(alg / (total_ms / 1e3) / 1e9, 1), "alg_frac": round(alg / (total_ms / 1e3) / 1e9 / peak, 4)}
 
