@@ -354,6 +354,27 @@ __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, c
     return act;
 }
 
+// Waves with round records (hcap > 0) keep the sources new at u in round
+// `round` as one whole block hist[round][u] -- a full 32-byte sector at
+// P = 4 -- where a direct output write would touch d different output
+// words (8 bytes each, partial sectors that the memory must read, merge and
+// write back when the neighbouring words of the sector arrive in other
+// rounds).  k_flush turns the records into the outputs after the wave;
+// rounds past the records write directly.  Returns the slots with new sources.
+template <int P>
+__device__ __forceinline__ unsigned int record_new(const Wave& w, uint32_t u, const uint64_t (&fw)[P], int round,
+                                                   const SlotDesc* ss) {
+    if (round < w.hcap) {
+        store_words<P>(w.hist + ((size_t)round * (size_t)w.n + u) * P, fw);
+        unsigned int act = 0;
+#pragma unroll
+        for (int s = 0; s < P; ++s)
+            if (fw[s]) act |= 1u << s;
+        return act;
+    }
+    return record_rows<P>(w, u, fw, round, ss);
+}
+
 // Pull result of v.  Fused (FUSE, the call's fused_pull): the vertex phase of
 // round rn = round + 1 is done on the spot -- the sources acc & ~vs are new
 // at v, they join vis[v], go to v's rows and to nwn[v], the next pull's
@@ -380,7 +401,7 @@ __device__ __forceinline__ bool pull_finish(const Wave& w, int32_t v, const uint
         for (int s = 0; s < P; ++s) nv[s] = vs[s] | nw[s];
         store_words<P>(w.vis + (size_t)v * P, nv);
         store_words<P>(nwn + (size_t)v * P, nw);
-        record_rows<P>(w, (uint32_t)v, nw, rn, w.slots);
+        record_new<P>(w, (uint32_t)v, nw, rn, w.slots);
     } else {
         store_words<P>(w.acc + (size_t)v * P, nw);
     }
@@ -454,7 +475,8 @@ __global__ void k_round_cond(Wave w, cudaGraphConditionalHandle h) {
     if (threadIdx.x != 0) return;
     const int r = *w.round_dev;
     unsigned int go = 0;
-    atomicAdd(w.iters, 1ull);
+    // one round; bits 40 and up count the rounds' k_flush launches (waves with round records)
+    atomicAdd(w.iters, w.hcap > 0 ? 1ull + (1ull << 40) : 1ull);
     if (w.ctl[r + 1].qlen > 0) {
         if (r + 2 < kMaxRounds) {
             *w.round_dev = r + 1;
@@ -501,11 +523,15 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
     const uint32_t* fbr = (round & 1) ? w.fb1 : w.fb0;  // F_round, set by its producers
     uint64_t* nwc = (round & 1) ? w.nw1 : w.nw0;        // F_round's new sources (pull gathers)
     {
-        // F_{round+1}'s bitmap was last read in round - 1: clear it for this round's edge phase
+        // F_{round+1}'s bitmap was last read in round - 1: clear it for this round's edge phase.
+        // With round records, F_round's bitmap (final now) is kept for k_flush
         uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
         const int64_t words = (w.n + 31) / 32;
-        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads)
+        uint32_t* keep = round < w.hcap ? w.fbh + (size_t)round * (size_t)words : nullptr;
+        for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < words; i += (int64_t)gridDim.x * kThreads) {
             fbn[i] = 0u;
+            if (keep) keep[i] = fbr[i];
+        }
     }
     if (fused && pull) return;  // nothing left of F_round's vertex phase
     const unsigned long long span = dense ? (unsigned long long)w.n : qlen;
@@ -551,7 +577,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                 store_words<P>(w.vis + (size_t)u * P, vs);
                 zero_words<P>(w.acc + (size_t)u * P);
                 if (!any) continue;
-                my_active |= record_rows<P>(w, u, fw[r], round, ss);
+                my_active |= record_new<P>(w, u, fw[r], round, ss);
                 my_nf += 1;
                 if (pull) {
                     if (pull_fused) store_words<P>(nwc + (size_t)u * P, fw[r]);  // the pull's gather source
@@ -957,6 +983,93 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
     }
 }
 
+// Outputs from the round records (Algorithm 1's Delta_v and S_v[i], read off
+// the rounds in which v carried new sources): for caller vertex v (internal
+// rank u), Delta of a slot is the first recorded round with sources of that
+// slot new at u, and S_v[i] is the record of round Delta + i, or empty when
+// u was not in that round's frontier.  Every output word is written, the
+// empty ones too, by the thread of v; the threads of a warp take consecutive
+// v, so the words of a sector are written within a few instructions of one
+// another.  at_cap: after phase A of round hcap - 1, rounds 0 .. hcap - 1
+// (later rounds then write their outputs directly, over what this wrote);
+// otherwise after the wave, its rounds -- unless the wave reached hcap - 1
+// (done then) or, with bound_round > 0, its frontier after bound_round rounds
+// was not empty (the wave runs again).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_flush(Wave w, const int32_t* iperm, int round, int at_cap,
+                                                     int bound_round) {
+    constexpr int U = P >= 8 ? 2 : 4;  // rounds whose records are loaded together
+    __shared__ SlotDesc ss[P];
+    __shared__ int s_rounds;
+    if (w.round_dev) round = *w.round_dev;
+    if (threadIdx.x == 0) {
+        int R = -1;
+        if (at_cap) {
+            if (round == w.hcap - 1 && w.ctl[round].qlen > 0) R = w.hcap;
+        } else if (!(bound_round > 0 && w.ctl[bound_round].qlen != 0)) {
+            int r = 0;
+            while (r < w.hcap && w.ctl[r].qlen > 0) ++r;
+            if (r < w.hcap) R = r;
+        }
+        s_rounds = R;
+    }
+    if (threadIdx.x < w.nslots) ss[threadIdx.x] = w.slots[threadIdx.x];
+    __syncthreads();
+    const int R = s_rounds;
+    if (R < 0) return;
+    const int64_t n = w.n;
+    const int d = w.d;
+    const size_t words = (size_t)((n + 31) / 32);
+    for (int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
+        const uint32_t u = iperm ? (uint32_t)iperm[v] : (uint32_t)v;
+        const uint32_t* fbu = w.fbh + (u >> 5);
+        const uint32_t bit = 1u << (u & 31);
+        int dl[P];
+        uint32_t wm[P];
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            dl[s] = -1;
+            wm[s] = 0;
+        }
+        for (int r0 = 0; r0 < R; r0 += U) {
+            bool in[U];
+            uint64_t x[U][P];
+#pragma unroll
+            for (int k = 0; k < U; ++k) in[k] = r0 + k < R && (fbu[(size_t)(r0 + k) * words] & bit);
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                if (in[k]) load_words<P>(w.hist + ((size_t)(r0 + k) * (size_t)n + u) * P, x[k]);
+                else {
+#pragma unroll
+                    for (int s = 0; s < P; ++s) x[k][s] = 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    if (s >= w.nslots || !x[k][s]) continue;
+                    if (dl[s] < 0) dl[s] = r0 + k;
+                    const int j = r0 + k - dl[s];
+                    if (j < d) {
+                        ss[s].masks[(size_t)j * (size_t)n + v] = x[k][s];
+                        wm[s] |= 1u << j;
+                    } else if (j > d) {
+                        set_status(w.status, CBFS_E_DIAMETER);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            if (s >= w.nslots) continue;
+            ss[s].dist[v] = dl[s] < 0 ? (uint8_t)0xFF : (uint8_t)dl[s];
+            for (int j = 0; j < d; ++j)
+                if (!((wm[s] >> j) & 1u)) ss[s].masks[(size_t)j * (size_t)n + v] = 0ull;
+        }
+    }
+}
+
 template __global__ void k_phase_a<1>(Wave, int);
 template __global__ void k_phase_a<2>(Wave, int);
 template __global__ void k_phase_a<4>(Wave, int);
@@ -973,6 +1086,10 @@ template __global__ void k_emit<1>(Wave, const int32_t*);
 template __global__ void k_emit<2>(Wave, const int32_t*);
 template __global__ void k_emit<4>(Wave, const int32_t*);
 template __global__ void k_emit<8>(Wave, const int32_t*);
+template __global__ void k_flush<1>(Wave, const int32_t*, int, int, int);
+template __global__ void k_flush<2>(Wave, const int32_t*, int, int, int);
+template __global__ void k_flush<4>(Wave, const int32_t*, int, int, int);
+template __global__ void k_flush<8>(Wave, const int32_t*, int, int, int);
 
 cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which, const int32_t* iperm) {
     switch (w.P) {
@@ -993,6 +1110,19 @@ cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, in
     }
     return cudaGetLastError();
 }
+
+cudaError_t launch_flush(const Wave& w, int round, int grid, cudaStream_t st, int at_cap, int bound_round,
+                         const int32_t* iperm) {
+    switch (w.P) {
+        case 1: k_flush<1><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+        case 2: k_flush<2><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+        case 4: k_flush<4><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+        case 8: k_flush<8><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 
 }  // namespace cbfs
 
@@ -1113,6 +1243,10 @@ struct cbfs_graph_s {
     uint16_t* wmask_r = nullptr; // per vertex and slot: which subset words the wave wrote
     uint64_t* masks_r = nullptr;
     int64_t masks_r_cap = 0;
+    uint64_t* hist = nullptr;    // round records of waves with fused pulls ([rounds][n][P])
+    int64_t hist_cap = 0;
+    uint32_t* fbh = nullptr;     // their frontier bitmaps ([rounds][bitmap words])
+    int64_t fbh_cap = 0;
     uint64_t* pull_pieces = nullptr;  // (rank << 32 | piece) of every vertex of degree > kPullMid
     int64_t n_small = 0, n_mid = 0, n_big = 0;  // degree classes of the default thresholds
     int64_t big_vertices = 0, big_pieces = 0;
@@ -1396,7 +1530,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
     cudaError_t e = cudaSuccess;
     for (size_t wv = 0; wv < waves.size() && e == cudaSuccess; ++wv) {
         const Wave& w = waves[wv];
-        const int P = w.P, d = w.d;
+        const int P = w.P;
         const int cnt = (int)(seed_off[wv + 1] - seed_off[wv]);
         e = cudaMemsetAsync(w.vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
@@ -1408,7 +1542,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         if (e == cudaSuccess) e = cudaMemsetAsync(w.ctl, 0, sizeof(RoundCtl) * kMaxRounds, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.round_dev, 0, sizeof(int), cs);
         if (e != cudaSuccess) break;
-        if (!w.dist_r) k_clear_outputs<<<grid, kThreads, 0, cs>>>(w);
+        if (!w.dist_r && !w.hcap) k_clear_outputs<<<grid, kThreads, 0, cs>>>(w);
         k_seed<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         // the round loop: a conditional WHILE node spliced into the capture
@@ -1433,6 +1567,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
             cudaSuccess)
             break;
         cudaError_t eb = launch_round(w, 0, grid, cs2, 0);
+        if (eb == cudaSuccess && w.hcap > 0) eb = launch_flush(w, 0, grid, cs2, 1, 0, g->iperm_d);  // at hcap - 1
         if (eb == cudaSuccess) eb = launch_round(w, 0, grid, cs2, 1);
         if (eb == cudaSuccess) {
             k_round_cond<<<1, 32, 0, cs2>>>(w, h);
@@ -1443,6 +1578,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         if (e == cudaSuccess) e = eb;
         if (e != cudaSuccess) break;
         if (w.dist_r && (e = launch_round(w, 0, grid, cs, 2, g->iperm_d)) != cudaSuccess) break;
+        if (!w.dist_r && w.hcap > 0 && (e = launch_flush(w, 0, grid, cs, 0, 0, g->iperm_d)) != cudaSuccess) break;
         k_check_sources<<<1, kThreads, 0, cs>>>(w, g->seeds + seed_off[wv], cnt, 0, nullptr);
         e = cudaGetLastError();
     }
@@ -1457,6 +1593,33 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         *out = nullptr;
         return CBFS_E_CUDA;
     }
+    return CBFS_OK;
+}
+
+// Rounds of round records for a wave with fused pulls (cbfs_tune_t
+// stage_rounds): < 0 none; > 0 that many (at most 255, so that a recorded
+// round is a valid Delta); 0 = as many as fit a quarter of the free device
+// memory (records already held count as free), at most kStageAuto.  Grows
+// the records to that size.
+int stage_rounds(cbfs_graph_s* g, const cbfs_tune_t* tune, int P, int* out) {
+    *out = 0;
+    const int64_t n = g->n;
+    int want = tune ? tune->stage_rounds : 0;
+    if (want < 0 || n == 0) return CBFS_OK;
+    const int64_t words = (n + 31) / 32;
+    const size_t per_round = sizeof(uint64_t) * (size_t)n * (size_t)P + sizeof(uint32_t) * (size_t)words;
+    if (want == 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        const size_t held = sizeof(uint64_t) * (size_t)g->hist_cap + sizeof(uint32_t) * (size_t)g->fbh_cap;
+        want = (int)std::min<size_t>((size_t)kStageAuto, (fr / 4 + held) / per_round);
+        if (want == 0) return CBFS_OK;
+    }
+    want = std::min(want, 255);
+    int rc = ensure_dev(&g->hist, &g->hist_cap, (int64_t)want * n * P);
+    if (!rc) rc = ensure_dev(&g->fbh, &g->fbh_cap, (int64_t)want * words);
+    if (rc) return rc;
+    *out = want;
     return CBFS_OK;
 }
 
@@ -1833,11 +1996,17 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.grid_a = g->grid_a[pi];
     w.fused_pull = (tune && tune->fused_pull > 0) ? 1 : 0;
     if (w.fused_pull) {
-        // no internal rows: the vertex phase (in the pull or in phase A) writes the
-        // slots' outputs directly, cleared per wave (k_clear_outputs); no emit
+        // no internal rows: the vertex phase (in the pull or in phase A) records each
+        // round's new sources (round records, then k_flush) or, past the records or
+        // without them, writes the slots' outputs directly (cleared per wave by
+        // k_clear_outputs); no emit
         w.dist_r = nullptr;
         w.masks_r = nullptr;
         w.wmask_r = nullptr;
+        rc = stage_rounds(g, tune, P, &w.hcap);
+        if (rc) return rc;
+        w.hist = g->hist;
+        w.fbh = g->fbh;
     }
 
     // Graph mode (device outputs): the call runs as one cached CUDA graph per
@@ -1928,7 +2097,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         // been copied out first (wave wv - G)
         if (!w.dist_r && host_out) CK(cudaStreamWaitEvent(st, g->ev_copy[wv % G], 0));
         int ev = prof_begin(g, 0, st);
-        if (!w.dist_r) k_clear_outputs<<<grid, kThreads, 0, st>>>(w);
+        if (!w.dist_r && !w.hcap) k_clear_outputs<<<grid, kThreads, 0, st>>>(w);
         k_seed<<<1, kThreads, 0, st>>>(w, g->seeds + wave_seed_off[wv], cnt);
         prof_end(g, ev, st);
         CK(cudaGetLastError());
@@ -1938,6 +2107,11 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                 ev = prof_begin(g, 1, st);
                 CK(launch_round(w, r, grid, st, 0));
                 prof_end(g, ev, st);
+                if (r == w.hcap - 1) {
+                    ev = prof_begin(g, 0, st);
+                    CK(launch_flush(w, r, grid, st, 1, 0, g->iperm_d));
+                    prof_end(g, ev, st);
+                }
                 ev = prof_begin(g, 2, st);
                 CK(launch_round(w, r, grid, st, 1));
                 prof_end(g, ev, st);
@@ -1949,6 +2123,11 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                 ev = prof_begin(g, 1, st);
                 CK(launch_round(w, r, grid, st, 0));
                 prof_end(g, ev, st);
+                if (r == w.hcap - 1) {
+                    ev = prof_begin(g, 0, st);
+                    CK(launch_flush(w, r, grid, st, 1, 0, g->iperm_d));
+                    prof_end(g, ev, st);
+                }
                 ev = prof_begin(g, 2, st);
                 CK(launch_round(w, r, grid, st, 1));
                 prof_end(g, ev, st);
@@ -1971,6 +2150,10 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         if (w.dist_r) {
             ev = prof_begin(g, 0, st);
             CK(launch_round(w, 0, grid, st, 2, g->iperm_d));
+            prof_end(g, ev, st);
+        } else if (w.hcap > 0) {
+            ev = prof_begin(g, 0, st);
+            CK(launch_flush(w, 0, grid, st, 0, bound, g->iperm_d));
             prof_end(g, ev, st);
         }
         if (host_out && (rerun || (wv + 1) % CG == 0 || wv == nwaves - 1)) {
@@ -2224,6 +2407,8 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
         if (hp.d != g->pull_pieces) dev_free(hp.d);
     dev_free(g->pull_pieces);
     dev_free(g->masks_r);
+    dev_free(g->hist);
+    dev_free(g->fbh);
     dev_free(g->ctl);
     dev_free(g->status);
     dev_free(g->slots);
@@ -2341,15 +2526,18 @@ int cbfs_host_free(void* host_ptr) {
 int cbfs_profile(cbfs_graph_t g, int enable, cbfs_kernel_times_t* host_out) {
     if (!g) return CBFS_E_INVALID;
     if (g->iters) {
-        // rounds run by graph-mode calls since the last read (three launches each)
+        // rounds run by graph-mode calls since the last read (three launches each, and
+        // a k_flush launch each in waves with round records: bits 40 and up)
         unsigned long long it = 0;
         CK(cudaSetDevice(g->device));
         CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(&it, g->iters, sizeof(it), cudaMemcpyDeviceToHost));
         CK(cudaMemset(g->iters, 0, sizeof(it)));
-        g->launches[1] += it;
-        g->launches[2] += it;
-        g->total_launches += 3ull * it;
+        const unsigned long long rounds = it & ((1ull << 40) - 1), flushes = it >> 40;
+        g->launches[0] += flushes;
+        g->launches[1] += rounds;
+        g->launches[2] += rounds;
+        g->total_launches += 3ull * rounds + flushes;
     }
     if (host_out) {
         for (int i = 0; i < 3; ++i) {

@@ -14,6 +14,7 @@ namespace cbfs {
 constexpr int kThreads = 256;       // threads per CTA of every traversal kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxSlots = 8;        // clusters in flight per wave: P in {1, 2, 4, 8}
+constexpr int kStageAuto = 96;      // round records kept by default (memory permitting)
 constexpr int kMaxRounds = 288;     // > 254 + 15 + 1: Delta < 255, offsets <= 15
 constexpr int64_t kBigDeg = 2048;   // push: longer lists are cut into pieces of this size
 constexpr int64_t kPullSmall = 32;  // pull: thread per vertex up to this degree
@@ -118,6 +119,10 @@ struct Wave {
                             // fused pulls, and the allocation-free entry point)
     uint16_t* wmask_r;      // [n][P] bit j: masks_r word j of the slot was written in this
                             // wave (started at the slot's first visit; never cleared)
+    uint64_t* hist;         // [hcap][n][P] round records of waves without rows: hist[i][u] =
+                            // the sources new at u in round i, valid iff bit u of fbh[i] is set
+    uint32_t* fbh;          // [hcap][bitmap words] F_i's bitmap, copied by phase A of round i
+    int hcap;               // rounds recorded (0: none, outputs written directly as they arise)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
     int grid_a;             // CTAs of the vertex phase (0: the edge phase's grid)
     int fused_pull;         // 1: pull rounds do their vertices' vertex phase on the spot
@@ -154,6 +159,11 @@ __global__ void k_phase_b(Wave w, int round);
 // Writes the wave's internal rows to the caller's cluster-major outputs.
 template <int P>
 __global__ void k_emit(Wave w, const int32_t* iperm);
+// Writes the outputs of a wave with round records (hcap > 0) from them:
+// at_cap != 0 after phase A of round hcap - 1 (later rounds write their
+// outputs directly), else after the wave when it ended before that round.
+template <int P>
+__global__ void k_flush(Wave w, const int32_t* iperm, int round, int at_cap, int bound_round);
 
 // Internal vertex order (cbfs_relabel.cu), computed on the device: ranks by
 // degree, highest first, ties to the smaller id; perm[rank] = id,
@@ -211,6 +221,9 @@ void labels_rollback(cbfs_labels_s* L, int base);
 // Launches phase A (which = 0), phase B (1) of one round, or the emit
 // kernel (2) for w.P (1, 2, 4 or 8).
 cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which, const int32_t* iperm = nullptr);
+// Launches k_flush for the wave (see there).
+cudaError_t launch_flush(const Wave& w, int round, int grid, cudaStream_t st, int at_cap, int bound_round,
+                         const int32_t* iperm);
 
 // Stream-ordered calls leave device-detected errors in their owner's status
 // word (a graph handle's or a label store's); cbfs_sync_status(stream) reads

@@ -112,6 +112,34 @@ def test_batched_equals_single_and_oracle(cb):
         assert (cb.as_numpy_u64(single[c][1]) == om).all()
 
 
+@pytest.mark.parametrize("stage_rounds", [-1, 1, 2, 5, 0])
+def test_fused_round_records_at_every_cap(cb, stage_rounds):
+    """Waves with fused pulls record each round's new sources and write the
+    outputs from the records after the wave; a wave with more rounds than
+    recorded writes them from the records at the cap and directly after it;
+    stage_rounds = -1 writes directly from the start (outputs cleared first).
+    Replayed graphs, host-driven rounds (bounded waves that may run again)
+    and eager pulls all equal the oracle on a road grid (tens of rounds) and
+    on R-MAT."""
+    for graph in ("grid", "rmat"):
+        if graph == "grid":
+            off, adj = I.road_grid(48, seed=I.MASTER_SEED + 2)
+            clusters, ds = I.ball_clusters(off, adj, 6, 16, seed=5)
+            d = max(ds)
+        else:
+            off, adj = I.rmat(12, seed=29)
+            clusters, d = I.star_clusters(off, adj, 6, seed=9, size="uniform")
+        g = cb.Graph(off, adj)
+        want = [O.cbfs_alg1(off, adj, S, d) for S in clusters]
+        for tune in ({"slots": 4}, {"slots": 2, "host_loop": 1}, dict(PULL_EAGER, slots=4)):
+            t = dict(tune, fused_pull=1, stage_rounds=stage_rounds)
+            for rep in range(2):
+                bd, bm = g.run_batched(clusters, d, tune=t)
+                for c, (od, om) in enumerate(want):
+                    assert (bd[c].cpu().numpy() == od).all(), (graph, t, rep, c)
+                    assert (cb.as_numpy_u64(bm[c]) == om).all(), (graph, t, rep, c)
+
+
 def test_waves_grouped_by_size_or_in_call_order(cb):
     """Clusters of mixed sizes: the default groups them into waves by size,
     wave_order = 1 keeps the call order; both, host-driven and replayed,
