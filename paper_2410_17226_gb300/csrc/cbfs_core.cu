@@ -400,7 +400,7 @@ __device__ __forceinline__ bool pull_finish(const Wave& w, int32_t v, const uint
 #pragma unroll
         for (int s = 0; s < P; ++s) nv[s] = vs[s] | nw[s];
         store_words<P>(w.vis + (size_t)v * P, nv);
-        store_words<P>(nwn + (size_t)v * P, nw);
+        if (rn >= w.hcap) store_words<P>(nwn + (size_t)v * P, nw);  // else its record is the gather source
         record_new<P>(w, (uint32_t)v, nw, rn, w.slots);
     } else {
         store_words<P>(w.acc + (size_t)v * P, nw);
@@ -556,7 +556,8 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
             const uint32_t u = dense ? (uint32_t)idx : q[idx];
             if (fused) {
                 // vis updated by the pull that produced F_round: record the rows
-                load_words<P>(nwc + (size_t)u * P, fw[r]);
+                load_words<P>(round < w.hcap ? w.hist + ((size_t)round * (size_t)w.n + u) * P : nwc + (size_t)u * P,
+                              fw[r]);
                 // (the fused pull recorded the rows too)
                 if (pull) continue;  // the dense edge phase needs no work lists
             } else {
@@ -580,7 +581,8 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                 my_active |= record_new<P>(w, u, fw[r], round, ss);
                 my_nf += 1;
                 if (pull) {
-                    if (pull_fused) store_words<P>(nwc + (size_t)u * P, fw[r]);  // the pull's gather source
+                    // the pull's gather source (a recorded round gathers from its record)
+                    if (pull_fused && round >= w.hcap) store_words<P>(nwc + (size_t)u * P, fw[r]);
                     continue;  // the dense edge phase needs no work lists
                 }
             }
@@ -669,7 +671,10 @@ __device__ __forceinline__ void pull_round(const Wave& w, RoundCtl* c, RoundCtl*
     const uint64_t* pieces = sparse_round ? w.pull_pieces_s : w.pull_pieces;
     const int64_t npieces = sparse_round ? w.n_pull_pieces_s : w.n_pull_pieces;
     const unsigned int active = c->slot_active;
-    const uint64_t* gsrc = FUSE ? ((round & 1) ? w.nw1 : w.nw0) : w.vis;  // gather source
+    // gather source: vis (plain); fused: the round's record, or nw past the records
+    const uint64_t* gsrc = !FUSE               ? w.vis
+                           : round < w.hcap ? w.hist + (size_t)round * (size_t)w.n * P
+                                            : ((round & 1) ? w.nw1 : w.nw0);
     uint64_t* nwn = (round & 1) ? w.nw0 : w.nw1;  // F_{round+1}'s new sources, written by pull_finish
     const int rn = round + 1;
     unsigned long long my_cnt = 0, my_sdeg = 0;
@@ -885,8 +890,12 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 3 : 4)) k_phase_b(Wave w, 
     const bool pull = c->mode != 0;
     // F_round's bitmap (read) and F_{round+1}'s (written by whoever adds a vertex;
     // phase A of this round cleared it)
-    // a dense frontier (over n/8) passes the membership test almost always: skip it then
-    const uint32_t* fb = (qlen * 8 > (unsigned long long)w.n) ? nullptr : ((round & 1) ? w.fb1 : w.fb0);
+    // a dense frontier (over n/8) passes the membership test almost always: skip it then,
+    // except in fused waves with round records, whose gather sources are not cleared per
+    // wave (a non-frontier entry may hold another wave's sources)
+    const bool test_all = FUSE && w.hcap > 0;
+    const uint32_t* fb =
+        (qlen * 8 > (unsigned long long)w.n && !test_all) ? nullptr : ((round & 1) ? w.fb1 : w.fb0);
     uint32_t* fbn = (round & 1) ? w.fb0 : w.fb1;
 
     if (!pull) {
@@ -996,7 +1005,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(Wave w, const int32_t* iperm)
 // (done then) or, with bound_round > 0, its frontier after bound_round rounds
 // was not empty (the wave runs again).
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_flush(Wave w, const int32_t* iperm, int round, int at_cap,
+__global__ void __launch_bounds__(kThreads, (P >= 8 ? 2 : 4)) k_flush(Wave w, const int32_t* iperm, int round, int at_cap,
                                                      int bound_round) {
     constexpr int U = P >= 8 ? 2 : 4;  // rounds whose records are loaded together
     __shared__ SlotDesc ss[P];
@@ -1023,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads) k_flush(Wave w, const int32_t* iperm
     for (int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
         const uint32_t u = iperm ? (uint32_t)iperm[v] : (uint32_t)v;
         const uint32_t* fbu = w.fbh + (u >> 5);
-        const uint32_t bit = 1u << (u & 31);
+        const int sh = (int)(u & 31);
         int dl[P];
         uint32_t wm[P];
 #pragma unroll
@@ -1031,31 +1040,43 @@ __global__ void __launch_bounds__(kThreads) k_flush(Wave w, const int32_t* iperm
             dl[s] = -1;
             wm[s] = 0;
         }
-        for (int r0 = 0; r0 < R; r0 += U) {
-            bool in[U];
-            uint64_t x[U][P];
+        for (int b0 = 0; b0 < R; b0 += 64) {
+            // the rounds of this block in which u was in the frontier, from
+            // independent bitmap loads; then their records, U at a time
+            const int nb = R - b0 < 64 ? R - b0 : 64;
+            uint64_t m = 0;
+#pragma unroll 8
+            for (int k = 0; k < 64; ++k)
+                if (k < nb) m |= (uint64_t)((fbu[(size_t)(b0 + k) * words] >> sh) & 1u) << k;
+            while (m) {
+                int rr[U];
+                uint64_t x[U][P];
 #pragma unroll
-            for (int k = 0; k < U; ++k) in[k] = r0 + k < R && (fbu[(size_t)(r0 + k) * words] & bit);
-#pragma unroll
-            for (int k = 0; k < U; ++k) {
-                if (in[k]) load_words<P>(w.hist + ((size_t)(r0 + k) * (size_t)n + u) * P, x[k]);
-                else {
-#pragma unroll
-                    for (int s = 0; s < P; ++s) x[k][s] = 0;
+                for (int k = 0; k < U; ++k) {
+                    rr[k] = m ? b0 + __ffsll((long long)m) - 1 : -1;
+                    m &= m - 1;
                 }
-            }
 #pragma unroll
-            for (int k = 0; k < U; ++k) {
+                for (int k = 0; k < U; ++k) {
+                    if (rr[k] >= 0) load_words<P>(w.hist + ((size_t)rr[k] * (size_t)n + u) * P, x[k]);
+                    else {
 #pragma unroll
-                for (int s = 0; s < P; ++s) {
-                    if (s >= w.nslots || !x[k][s]) continue;
-                    if (dl[s] < 0) dl[s] = r0 + k;
-                    const int j = r0 + k - dl[s];
-                    if (j < d) {
-                        ss[s].masks[(size_t)j * (size_t)n + v] = x[k][s];
-                        wm[s] |= 1u << j;
-                    } else if (j > d) {
-                        set_status(w.status, CBFS_E_DIAMETER);
+                        for (int s = 0; s < P; ++s) x[k][s] = 0;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+#pragma unroll
+                    for (int s = 0; s < P; ++s) {
+                        if (s >= w.nslots || !x[k][s]) continue;
+                        if (dl[s] < 0) dl[s] = rr[k];
+                        const int j = rr[k] - dl[s];
+                        if (j < d) {
+                            ss[s].masks[(size_t)j * (size_t)n + v] = x[k][s];
+                            wm[s] |= 1u << j;
+                        } else if (j > d) {
+                            set_status(w.status, CBFS_E_DIAMETER);
+                        }
                     }
                 }
             }
@@ -1534,7 +1555,7 @@ int build_graph(cbfs_graph_s* g, const std::vector<Wave>& waves, const std::vect
         const int cnt = (int)(seed_off[wv + 1] - seed_off[wv]);
         e = cudaMemsetAsync(w.vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, cs);
-        if (e == cudaSuccess && w.fused_pull)  // a fused pull round may read any vertex's entry
+        if (e == cudaSuccess && w.fused_pull && !w.hcap)  // a fused pull round may read any vertex's entry
             e = cudaMemsetAsync(w.nw0, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.rq, 0, sizeof(uint32_t) * (size_t)n, cs);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.fb0, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, cs);
@@ -2086,7 +2107,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         w.slots = g->slots + (size_t)wv * P;
         CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
-        if (w.fused_pull)  // a fused pull round may read any vertex's entry
+        if (w.fused_pull && !w.hcap)  // a fused pull round may read any vertex's entry
             CK(cudaMemsetAsync(g->nw, 0, sizeof(uint64_t) * 2 * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->rq, 0, sizeof(uint32_t) * (size_t)n, st));
         CK(cudaMemsetAsync(g->fb, 0, sizeof(uint32_t) * 2 * (size_t)bm_words, st));

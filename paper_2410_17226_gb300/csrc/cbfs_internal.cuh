@@ -87,7 +87,10 @@ struct Wave {
     uint64_t* acc;          // [n][P]
     uint64_t* nw0;          // [n][P] sources new at v in round i, for i even / odd: written by
     uint64_t* nw1;          //   the vertex phase of v (in phase A, or in the pull of round i-1)
-                            //   and gathered by the pull of round i; cleared per wave
+                            //   and gathered by the pull of round i of a fused wave; cleared per
+                            //   wave, except in waves with round records (hcap > 0), which
+                            //   gather from the record of a recorded round and use nw only
+                            //   past them, always through the frontier bitmap
     uint32_t* piece_cnt;    // [n] pull pieces of a hub done this round (the last one resets it)
     uint32_t* rq;           // [n] queue claim stamps: F_i holds v iff rq[v] was set to i+1
     uint32_t* q0;           // frontier queues of vertex ids
