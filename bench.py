@@ -1026,6 +1026,9 @@ def summary_of(line: dict) -> dict:
     if rg:
         out["road_grid_4096"] = {"gteps": rg["gteps"], "alg_frac": rg["alg_frac"], "ms": rg["ms_all_clusters"],
                                  "garcs_per_s": round(rg["arcs_per_s"] / 1e9, 1)}
+    # share of slot-rounds in which a wave's cluster still had work (lockstep waves)
+    out["lockstep_busy"] = [get("lockstep", "busy_slot_round_share"),
+                            get("next", "road_grid", "lockstep", "busy_slot_round_share")]
     lc = get("configs", "label_construction_s24")
     if lc:
         out["labels_s24_1024"] = {"traversal_ms": lc["traversal_ms"], "alg_frac": lc["alg_frac"],

@@ -70,3 +70,22 @@ def test_product_path_has_no_cpu_fallback():
 
         with pytest.raises(RuntimeError):
             cbfs.Graph([0, 0], [])
+
+
+def _struct_fields(name):
+    """(type, field) pairs of a typedef'd struct in include/cbfs.h, in order."""
+    with open(os.path.join(ROOT, "include", "cbfs.h")) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    body = re.search(r"typedef struct \w*\s*\{([^{}]*)\}\s*" + name + r"\s*;", text).group(1)
+    return re.findall(r"(\w+)\s+(\w+)\s*;", body)
+
+
+def test_python_structs_match_the_header_field_by_field():
+    import ctypes
+
+    from paper_2410_17226_gb300 import cbfs
+
+    ctype = {"float": ctypes.c_float, "int": ctypes.c_int, "uint64_t": ctypes.c_uint64}
+    for py, c in ((cbfs.Tune, "cbfs_tune_t"), (cbfs.ClusterStats, "cbfs_cluster_stats_t")):
+        want = [(f, ctype[t]) for t, f in _struct_fields(c)]
+        assert [(f, t) for f, t in py._fields_] == want, c

@@ -43,14 +43,17 @@ def valid_columns(rows, count, cap, d):
     return np.concatenate(parts, axis=1)
 
 
-@pytest.mark.parametrize("slots,host_loop,fused", [(1, 0, 0), (2, 1, 0), (4, 0, 0), (8, 0, 0), (4, 0, 1), (2, 1, 1)])
-def test_host_outputs_equal_device_outputs(cb, slots, host_loop, fused):
-    """fused: fused pulls, whose waves write their outputs directly (into the
-    staging ring for host outputs) instead of emitting internal rows."""
+@pytest.mark.parametrize("slots,host_loop,fused,stage", [(1, 0, 0, 0), (2, 1, 0, 0), (4, 0, 0, 0), (8, 0, 0, 0),
+                                                        (4, 0, 1, 0), (2, 1, 1, 0), (4, 1, 1, 2), (4, 0, 1, -1)])
+def test_host_outputs_equal_device_outputs(cb, slots, host_loop, fused, stage):
+    """fused: fused pulls, whose waves write their outputs (into the staging
+    ring for host outputs) from their round records after the wave, or with
+    stage = 2 from two rounds of records and directly after them, or with
+    stage = -1 directly as they arise, instead of emitting internal rows."""
     off, adj = I.rmat(12, seed=5)
     clusters, d = I.star_clusters(off, adj, 19, seed=3, size="uniform")
     g = cb.Graph(off, adj)
-    tune = {"slots": slots, "host_loop": host_loop, "fused_pull": fused}
+    tune = {"slots": slots, "host_loop": host_loop, "fused_pull": fused, "stage_rounds": stage}
     dd, dm = g.run_batched(clusters, d, tune=tune)
     C, n = len(clusters), g.n
     ref_d, ref_m = dd.cpu(), dm.cpu()
@@ -186,12 +189,14 @@ def test_degree_order_on_skewed_graphs(cb, shape):
         assert (dist[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(masks[c]) == om).all()
 
 
-@pytest.mark.parametrize("slots,fused", [(1, 0), (2, 0), (2, 1)])
-def test_labels_and_host_outputs_with_rerun_waves(cb, slots, fused):
+@pytest.mark.parametrize("slots,fused,stage", [(1, 0, 0), (2, 0, 0), (2, 1, 0), (2, 1, 3)])
+def test_labels_and_host_outputs_with_rerun_waves(cb, slots, fused, stage):
     """Waves deeper than the first are traversed again at the end of the call
     (host-driven rounds); their host copies and label rows are rewritten.
     With one cluster per wave the label groups span many waves.  fused: the
-    waves write their outputs directly into the staging ring."""
+    waves write their outputs into the staging ring from their round records
+    (96 rounds by default, 3 with stage = 3: waves of up to 239 rounds are
+    flushed at the last recorded round and write directly after it)."""
     off, adj = I.path(240)
     g = cb.Graph(off, adj)
     base = [np.array([120, 121], np.int32), np.array([0, 1], np.int32), np.array([60], np.int32),
@@ -201,14 +206,15 @@ def test_labels_and_host_outputs_with_rerun_waves(cb, slots, fused):
     L = cb.Labels(n, C, d)
     hd = torch.empty((C, n), dtype=torch.uint8).pin_memory()
     hm = torch.empty((C, d, n), dtype=torch.int64).pin_memory()
-    g.run_batched_labels(clusters, d, L, dist=hd, masks=hm, tune={"slots": slots, "fused_pull": fused})
+    tune = {"slots": slots, "fused_pull": fused, "stage_rounds": stage}
+    g.run_batched_labels(clusters, d, L, dist=hd, masks=hm, tune=tune)
     od = np.zeros((C, n), np.uint8)
     om = np.zeros((C, d, n), np.uint64)
     for c, S in enumerate(clusters):
         od[c], om[c] = O.cbfs_alg1(off, adj, S, d)
     assert (hd.numpy() == od).all() and (hm.numpy().view(np.uint64) == om).all()
     L2 = cb.Labels(n, C, d)
-    g.run_batched_labels(clusters, d, L2, tune={"slots": slots, "fused_pull": fused})  # labels only (wave ring)
+    g.run_batched_labels(clusters, d, L2, tune=tune)  # labels only (wave ring)
     L3 = cb.Labels(n, C, d)
     L3.append(torch.from_numpy(od).cuda(), torch.from_numpy(om.view(np.int64)).cuda(), [len(S) for S in clusters])
     ref = valid_columns(rows_of(L3, n), C, C, d)
