@@ -228,6 +228,30 @@ def test_edge_cases(cb):
     check_one(cb, g, off, adj, np.array([0, 1, 2], np.int32), 2)
 
 
+@pytest.mark.parametrize("stage", [0, 2, 200, -1])
+def test_fused_waves_report_depth_and_diameter(cb, stage):
+    """Fused waves with round records: a first visit past distance 254 and a
+    source pair farther apart than d are reported whether the outputs come
+    from the records (stage 0 = default, 200), from two rounds of records and
+    then directly (2), or directly (-1); the deepest representable distance,
+    254, still works, and a call after an error on the same handle is exact."""
+    off, adj = I.path(300)
+    g = cb.Graph(off, adj)
+    for host_loop, alpha in ((0, 0.0), (1, 0.0), (0, 1e-9), (1, 1e-9)):  # pushes on a path, or pulls
+        tune = {"slots": 1, "fused_pull": 1, "stage_rounds": stage, "host_loop": host_loop, "pull_alpha": alpha}
+        with pytest.raises(cb.CbfsError) as e:
+            g.run_batched([np.array([0], np.int32)], 0, tune=tune)
+        assert e.value.code == cb.E_DEPTH
+        with pytest.raises(cb.CbfsError) as e:
+            g.run_batched([np.array([10, 14], np.int32)], 2, tune=tune)
+        assert e.value.code == cb.E_DIAMETER
+        check_one(cb, g, off, adj, np.array([45, 46, 47], np.int32), 2, tune)
+    off, adj = I.path(255)
+    g = cb.Graph(off, adj)
+    check_one(cb, g, off, adj, np.array([0, 1, 2], np.int32), 2,
+              {"slots": 2, "fused_pull": 1, "stage_rounds": stage, "pull_alpha": 1e-9})
+
+
 def test_error_paths(cb):
     off, adj = I.path(300)
     g = cb.Graph(off, adj)
