@@ -2161,9 +2161,14 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
                 rounds = r + 1;
             }
             if (!done) {
+                // the call fails here: it returns (and clears) the status word like any
+                // blocking call, so the next call does not report the same error again
+                int status = 0;
+                CK(cudaMemcpyAsync(&status, g->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaMemsetAsync(g->status, 0, sizeof(int), st));
                 CK(cudaStreamSynchronize(st));
                 prof_collect(g);
-                return CBFS_E_DEPTH;
+                return status ? status : CBFS_E_DEPTH;
             }
         }
         const int b = wv % G;

@@ -234,7 +234,8 @@ def test_fused_waves_report_depth_and_diameter(cb, stage):
     source pair farther apart than d are reported whether the outputs come
     from the records (stage 0 = default, 200), from two rounds of records and
     then directly (2), or directly (-1); the deepest representable distance,
-    254, still works, and a call after an error on the same handle is exact."""
+    254, still works, and a call after an error on the same handle is exact
+    (an error a call returns is not reported again by the next one)."""
     off, adj = I.path(300)
     g = cb.Graph(off, adj)
     for host_loop, alpha in ((0, 0.0), (1, 0.0), (0, 1e-9), (1, 1e-9)):  # pushes on a path, or pulls
