@@ -290,9 +290,19 @@ __device__ __forceinline__ unsigned int unfinished(const uint64_t (&vs)[P], cons
 // perm[u] (identity when perm is null); those outputs were cleared to
 // Delta = 0xFF and empty subsets before the wave.  Returns the slots with
 // new sources.
+// The P Delta bytes of u's internal row in one load (the row starts at a
+// multiple of P bytes).
+template <int P>
+__device__ __forceinline__ uint64_t load_delta_row(const uint8_t* p) {
+    if constexpr (P == 1) return *p;
+    else if constexpr (P == 2) return *reinterpret_cast<const uint16_t*>(p);
+    else if constexpr (P == 4) return *reinterpret_cast<const uint32_t*>(p);
+    else return *reinterpret_cast<const unsigned long long*>(p);
+}
+
 template <int P>
 __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, const uint64_t (&fw)[P], int round,
-                                                    const SlotDesc* ss) {
+                                                    const SlotDesc* ss, const uint64_t* dpre = nullptr) {
     unsigned int act = 0;
     if (w.dist_r) {
         // the wave's internal rows of u: P Delta bytes, then each slot's d
@@ -303,7 +313,8 @@ __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, c
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             if (!fw[s]) continue;
-            const uint8_t dd = dr[s];
+            // Delta of the slot: from the row's bytes loaded by the caller, if it did
+            const uint8_t dd = dpre ? (uint8_t)(*dpre >> (8 * s)) : dr[s];
             int j;
             uint32_t wm;
             if (dd == 0xFF) {
@@ -363,7 +374,7 @@ __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, c
 // rounds past the records write directly.  Returns the slots with new sources.
 template <int P>
 __device__ __forceinline__ unsigned int record_new(const Wave& w, uint32_t u, const uint64_t (&fw)[P], int round,
-                                                   const SlotDesc* ss) {
+                                                   const SlotDesc* ss, const uint64_t* dpre = nullptr) {
     if (round < w.hcap) {
         store_words<P>(w.hist + ((size_t)round * (size_t)w.n + u) * P, fw);
         unsigned int act = 0;
@@ -372,7 +383,7 @@ __device__ __forceinline__ unsigned int record_new(const Wave& w, uint32_t u, co
             if (fw[s]) act |= 1u << s;
         return act;
     }
-    return record_rows<P>(w, u, fw, round, ss);
+    return record_rows<P>(w, u, fw, round, ss, dpre);
 }
 
 // Pull result of v.  Fused (FUSE, the call's fused_pull): the vertex phase of
@@ -561,13 +572,16 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                 // (the fused pull recorded the rows too)
                 if (pull) continue;  // the dense edge phase needs no work lists
             } else {
+                // u's acc, vis and (with internal rows) Delta bytes, loaded together: a
+                // member of F_round always has sources in acc
                 uint64_t a[P], vs[P];
                 load_words<P>(w.acc + (size_t)u * P, a);
+                load_words<P>(w.vis + (size_t)u * P, vs);
+                const uint64_t dpre = w.dist_r ? load_delta_row<P>(w.dist_r + (size_t)u * P) : 0ull;
                 uint64_t anyacc = 0;
 #pragma unroll
                 for (int s = 0; s < P; ++s) anyacc |= a[s];
                 if (!anyacc) continue;  // not in F_round (dense scan), or nothing new
-                load_words<P>(w.vis + (size_t)u * P, vs);
                 uint64_t any = 0;
 #pragma unroll
                 for (int s = 0; s < P; ++s) {
@@ -578,7 +592,7 @@ __global__ void __launch_bounds__(kThreads) k_phase_a(Wave w, int round) {
                 store_words<P>(w.vis + (size_t)u * P, vs);
                 zero_words<P>(w.acc + (size_t)u * P);
                 if (!any) continue;
-                my_active |= record_new<P>(w, u, fw[r], round, ss);
+                my_active |= record_new<P>(w, u, fw[r], round, ss, w.dist_r ? &dpre : nullptr);
                 my_nf += 1;
                 if (pull) {
                     // the pull's gather source (a recorded round gathers from its record)
