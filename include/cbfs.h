@@ -127,6 +127,13 @@ typedef struct cbfs_tune_s {
        0 = default: as many as fit a quarter of the free device memory, at
        most 96; > 0 = that many (at most 255); < 0 = none. */
     int stage_rounds;
+    /* calls with device outputs: clusters that fill only part of a 64-bit
+       slot word share words (largest first, each into the fullest word with
+       room, at most 31 to a word), so a wave traverses as many clusters as
+       its words hold; each cluster's outputs are read off its bits of the
+       round records.  Used when it saves words and round records fit.
+       0 = default (on); < 0 = one cluster per word. */
+    int pack;
 } cbfs_tune_t;
 
 /* Work counters of one cluster's traversal (Theorem 1). */

@@ -40,7 +40,7 @@ class Tune(ctypes.Structure):
     _fields_ = [("pull_alpha", ctypes.c_float), ("slots", ctypes.c_int), ("dense_div", ctypes.c_int),
                 ("host_loop", ctypes.c_int), ("small_deg", ctypes.c_int), ("mid_deg", ctypes.c_int),
                 ("sparse_mid_deg", ctypes.c_int), ("wave_order", ctypes.c_int), ("fused_pull", ctypes.c_int),
-                ("stage_rounds", ctypes.c_int)]
+                ("stage_rounds", ctypes.c_int), ("pack", ctypes.c_int)]
 
 
 class KernelTimes(ctypes.Structure):
@@ -263,6 +263,7 @@ class Graph:
             t.wave_order = int(tune.get("wave_order", 0))
             t.fused_pull = int(tune.get("fused_pull", 0))
             t.stage_rounds = int(tune.get("stage_rounds", 0))
+            t.pack = int(tune.get("pack", 0))
         return t
 
     def run_batched(self, clusters: Sequence | None, d: int, dist: torch.Tensor | None = None,

@@ -341,6 +341,36 @@ __device__ __forceinline__ unsigned int record_rows(const Wave& w, uint32_t u, c
             }
             act |= 1u << s;
         }
+    } else if (w.nmembers) {
+        // direct, packed wave: each member cluster's output, from its bits of the word
+        const size_t id = w.perm ? (size_t)w.perm[u] : (size_t)u;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            uint64_t x = fw[s];
+            if (x) act |= 1u << s;
+            while (x) {
+                const int b = __ffsll((long long)x) - 1;
+                const unsigned int mi = w.bit_member[s * 64 + b];
+                if (mi >= (unsigned int)w.nmembers) {  // never for member tables built by the host
+                    set_status(w.status, CBFS_E_INVALID);
+                    break;
+                }
+                const MemberDesc& M = w.members[mi];
+                x &= ~(M.mask | (1ull << b));  // bit b always goes: the loop ends whatever the tables hold
+                const uint64_t bits = (fw[s] & M.mask) >> M.off;
+                const uint8_t dd = M.dist[id];
+                int j;
+                if (dd == 0xFF) {
+                    if (round >= 255) set_status(w.status, CBFS_E_DEPTH);
+                    else M.dist[id] = (uint8_t)round;
+                    j = 0;
+                } else {
+                    j = round - (int)dd;
+                }
+                if (j < w.d) M.masks[(size_t)j * (size_t)w.n + id] = bits;
+                else if (j > w.d) set_status(w.status, CBFS_E_DIAMETER);
+            }
+        }
     } else {
         // direct: each slot's cluster-major output at the caller's id
         const size_t id = w.perm ? (size_t)w.perm[u] : (size_t)u;
@@ -440,7 +470,8 @@ __global__ void k_seed(Wave w, const uint64_t* seeds, int count) {
             set_status(w.status, CBFS_E_INVALID);
             continue;
         }
-        w.acc[(size_t)v * w.P + s] = 1ull << j;  // (v, s) is unique within a wave
+        // packed clusters of one word may share a source vertex
+        atomicOr(reinterpret_cast<unsigned long long*>(w.acc + (size_t)v * w.P + s), 1ull << j);
         if (atomicExch(w.rq + v, 1u) != 1u) {
             append(w.q0, &w.ctl[0].qlen, v);
             atomicAdd(&w.ctl[0].sdeg, (unsigned long long)(w.off[v + 1] - w.off[v]));
@@ -464,7 +495,9 @@ __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count, int bo
         const int s = (int)((e >> 40) & 0xFF);
         const uint32_t v = (uint32_t)e;
         if ((int64_t)v >= w.n || s >= w.P) continue;  // flagged by k_seed
-        if (w.vis[(size_t)v * w.P + s] != w.slots[s].all) set_status(w.status, CBFS_E_DIAMETER);
+        // each cluster's sources must have seen all of that cluster's sources
+        const uint64_t want = w.nmembers ? w.members[(e >> 48) & 0xFF].mask : w.slots[s].all;
+        if ((w.vis[(size_t)v * w.P + s] & want) != want) set_status(w.status, CBFS_E_DIAMETER);
     }
 }
 
@@ -1105,6 +1138,130 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 2 : 4)) k_flush(Wave w, co
     }
 }
 
+// k_flush for packed waves: a slot word holds several clusters (members),
+// each a contiguous range of its bits.  Caller vertex v's outputs of every
+// member come from the same round records, masked to the member's bits and
+// shifted down to its own bit order: Delta is the first recorded round with
+// bits of the member new at u, S_v[i] the member's bits of the record of
+// round Delta + i.  Word by word, a thread keeps each member's Delta and
+// written-word mask in shared memory; the bits of a record are taken member
+// by member (the member of a bit comes from the wave's bit table).
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_flush_packed(Wave w, const int32_t* iperm, int round, int at_cap,
+                                                            int bound_round) {
+    constexpr int U = 4;
+    __shared__ MemberDesc sm[P * kWordMembers];
+    __shared__ uint8_t sbit[P * 64];
+    __shared__ uint8_t sdl[kWordMembers][kThreads];
+    __shared__ uint16_t swm[kWordMembers][kThreads];
+    __shared__ int s_first[P + 1];
+    __shared__ int s_rounds;
+    if (w.round_dev) round = *w.round_dev;
+    if (threadIdx.x == 0) {
+        int R = -1;
+        if (at_cap) {
+            if (round == w.hcap - 1 && w.ctl[round].qlen > 0) R = w.hcap;
+        } else if (!(bound_round > 0 && w.ctl[bound_round].qlen != 0)) {
+            int r = 0;
+            while (r < w.hcap && w.ctl[r].qlen > 0) ++r;
+            if (r < w.hcap) R = r;
+        }
+        s_rounds = R;
+    }
+    const int nm = w.nmembers < P * kWordMembers ? w.nmembers : P * kWordMembers;
+    for (int i = threadIdx.x; i < nm; i += kThreads) sm[i] = w.members[i];
+    for (int i = threadIdx.x; i < P * 64; i += kThreads) sbit[i] = w.bit_member[i];
+    if (threadIdx.x <= P) {
+        // members are stored word by word: word s holds [s_first[s], s_first[s + 1])
+        int f = nm;
+        for (int i = 0; i < nm; ++i)
+            if (w.members[i].word >= (int)threadIdx.x) {
+                f = i;
+                break;
+            }
+        s_first[threadIdx.x] = f;
+    }
+    __syncthreads();
+    const int R = s_rounds;
+    if (R < 0) return;
+    const int64_t n = w.n;
+    const int d = w.d;
+    const size_t words = (size_t)((n + 31) / 32);
+    const int t = threadIdx.x;
+    for (int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x; v < n; v += (int64_t)gridDim.x * kThreads) {
+        const uint32_t u = iperm ? (uint32_t)iperm[v] : (uint32_t)v;
+        const uint32_t* fbu = w.fbh + (u >> 5);
+        const int sh = (int)(u & 31);
+        // the rounds in which u was in the frontier (R <= 255: four 64-bit blocks)
+        uint64_t mk[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int nb = R - 64 * b;
+            if (nb <= 0) continue;
+#pragma unroll 8
+            for (int k = 0; k < 64; ++k)
+                if (k < nb) mk[b] |= (uint64_t)((fbu[(size_t)(64 * b + k) * words] >> sh) & 1u) << k;
+        }
+        for (int s = 0; s < w.nslots; ++s) {
+            const int m0 = s_first[s], mc = s_first[s + 1] - m0;
+            for (int i = 0; i < mc; ++i) {
+                sdl[i][t] = 0xFF;
+                swm[i][t] = 0;
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                uint64_t m = mk[b];
+                while (m) {
+                    int rr[U];
+                    uint64_t x[U];
+#pragma unroll
+                    for (int k = 0; k < U; ++k) {
+                        rr[k] = m ? 64 * b + __ffsll((long long)m) - 1 : -1;
+                        m &= m - 1;
+                    }
+#pragma unroll
+                    for (int k = 0; k < U; ++k)
+                        x[k] = rr[k] >= 0 ? w.hist[((size_t)rr[k] * (size_t)n + u) * P + s] : 0ull;
+#pragma unroll
+                    for (int k = 0; k < U; ++k) {
+                        uint64_t left = x[k];
+                        while (left) {
+                            const int bt = __ffsll((long long)left) - 1;
+                            const int i = (int)sbit[s * 64 + bt] - m0;
+                            if (i < 0 || i >= mc) {  // a bit outside every member: never for host-built tables
+                                set_status(w.status, CBFS_E_INVALID);
+                                break;
+                            }
+                            const MemberDesc& M = sm[m0 + i];
+                            left &= ~(M.mask | (1ull << bt));  // bit bt always goes: the loop ends
+                            const uint64_t bits = (x[k] & M.mask) >> M.off;
+                            int dl = sdl[i][t];
+                            if (dl == 0xFF) {
+                                dl = rr[k];
+                                sdl[i][t] = (uint8_t)dl;
+                            }
+                            const int j = rr[k] - dl;
+                            if (j < d) {
+                                M.masks[(size_t)j * (size_t)n + v] = bits;
+                                swm[i][t] = (uint16_t)(swm[i][t] | (1u << j));
+                            } else if (j > d) {
+                                set_status(w.status, CBFS_E_DIAMETER);
+                            }
+                        }
+                    }
+                }
+            }
+            for (int i = 0; i < mc; ++i) {
+                const MemberDesc& M = sm[m0 + i];
+                M.dist[v] = sdl[i][t];
+                const uint32_t wm = swm[i][t];
+                for (int j = 0; j < d; ++j)
+                    if (!((wm >> j) & 1u)) M.masks[(size_t)j * (size_t)n + v] = 0ull;
+            }
+        }
+    }
+}
+
 template __global__ void k_phase_a<1>(Wave, int);
 template __global__ void k_phase_a<2>(Wave, int);
 template __global__ void k_phase_a<4>(Wave, int);
@@ -1125,6 +1282,10 @@ template __global__ void k_flush<1>(Wave, const int32_t*, int, int, int);
 template __global__ void k_flush<2>(Wave, const int32_t*, int, int, int);
 template __global__ void k_flush<4>(Wave, const int32_t*, int, int, int);
 template __global__ void k_flush<8>(Wave, const int32_t*, int, int, int);
+template __global__ void k_flush_packed<1>(Wave, const int32_t*, int, int, int);
+template __global__ void k_flush_packed<2>(Wave, const int32_t*, int, int, int);
+template __global__ void k_flush_packed<4>(Wave, const int32_t*, int, int, int);
+template __global__ void k_flush_packed<8>(Wave, const int32_t*, int, int, int);
 
 cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, int which, const int32_t* iperm) {
     switch (w.P) {
@@ -1148,6 +1309,16 @@ cudaError_t launch_round(const Wave& w, int round, int grid, cudaStream_t st, in
 
 cudaError_t launch_flush(const Wave& w, int round, int grid, cudaStream_t st, int at_cap, int bound_round,
                          const int32_t* iperm) {
+    if (w.nmembers) {
+        switch (w.P) {
+            case 1: k_flush_packed<1><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+            case 2: k_flush_packed<2><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+            case 4: k_flush_packed<4><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+            case 8: k_flush_packed<8><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (w.P) {
         case 1: k_flush<1><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
         case 2: k_flush<2><<<grid, kThreads, 0, st>>>(w, iperm, round, at_cap, bound_round); break;
@@ -1323,6 +1494,10 @@ struct cbfs_graph_s {
     int64_t slots_cap = 0;
     uint64_t* seeds = nullptr;
     int64_t seeds_cap = 0;
+    MemberDesc* members = nullptr;  // packed waves: member tables and bit tables of a call
+    int64_t members_cap = 0;
+    uint8_t* bitm = nullptr;
+    int64_t bitm_cap = 0;
     // pinned host staging: the slot tables and seeds of a call are uploaded
     // from ring entry (call number % kUploadRing); a call waits for the upload
     // of the call kUploadRing calls earlier before it rewrites that entry, so
@@ -1335,6 +1510,10 @@ struct cbfs_graph_s {
         int64_t slots_cap = 0;
         uint64_t* seeds = nullptr;
         int64_t seeds_cap = 0;
+        MemberDesc* members = nullptr;
+        int64_t members_cap = 0;
+        uint8_t* bitm = nullptr;
+        int64_t bitm_cap = 0;
         cudaEvent_t done = nullptr;
     };
     Upload up[kUploadRing];
@@ -1836,12 +2015,20 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     // order[pos]: the cluster in wave pos / P, slot pos % P (set below)
     std::vector<int> order((size_t)C);
     for (int c = 0; c < C; ++c) order[c] = c;
+    // packed waves: the bits used in each slot word (set below); a word's
+    // pull stops once all of its bits are in, as one cluster of that size
+    std::vector<int> word_bits;
     auto wave_alpha = [&](int wv) -> float {
         if (alpha_given) return alpha;
         int max_k = 0;
-        for (int pos = wv * P; pos < std::min(C, (wv + 1) * P); ++pos) {
-            const int c = order[pos];
-            max_k = std::max(max_k, coff[c + 1] - coff[c]);
+        if (!word_bits.empty()) {
+            for (int pos = wv * P; pos < std::min((int)word_bits.size(), (wv + 1) * P); ++pos)
+                max_k = std::max(max_k, word_bits[pos]);
+        } else {
+            for (int pos = wv * P; pos < std::min(C, (wv + 1) * P); ++pos) {
+                const int c = order[pos];
+                max_k = std::max(max_k, coff[c + 1] - coff[c]);
+            }
         }
         return max_k <= 4 ? 0.02f : 0.08f;
     };
@@ -1868,7 +2055,7 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     if (rc) return rc;
     const int pi = P == 1 ? 0 : P == 2 ? 1 : P == 4 ? 2 : 3;
     const int grid = g->grid_p[pi];
-    const int nwaves = (C + P - 1) / P;
+    int nwaves = (C + P - 1) / P;  // slot words / P once packing has been decided
     const int64_t total_src = coff[C];
     const int64_t n = g->n;
     // Where each wave's outputs go.  Device outputs: straight into dist/masks.
@@ -1909,6 +2096,66 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     if (!staged && !L && !(tune && tune->wave_order == 1))
         std::stable_sort(order.begin(), order.end(),
                          [&](int a, int b) { return coff[a + 1] - coff[a] > coff[b + 1] - coff[b]; });
+    // Packed waves.  With device outputs and round records, clusters whose
+    // sources fill only part of a 64-bit slot word share words: every bit of a
+    // word is an independent BFS, so the traversal is that of the words, and
+    // each cluster's outputs are its range of bits in the round records
+    // (k_flush_packed).  Clusters go to words by best fit, largest first (the
+    // fullest word with room, a new word otherwise), at most kWordMembers to a
+    // word; the words fill the waves in that order.  Used when it saves words.
+    const bool fused = tune && tune->fused_pull > 0;
+    const bool want_pack = !staged && !L && C > 1 && !(tune && (tune->wave_order == 1 || tune->pack < 0));
+    std::vector<int> word_first;             // packed: word i holds wmem[word_first[i] .. word_first[i + 1])
+    std::vector<std::pair<int, int>> wmem;   // (cluster, bit offset)
+    if (want_pack) {
+        std::vector<std::vector<std::pair<int, int>>> words;
+        std::vector<int> used;
+        std::vector<std::vector<int>> by_free(65);  // words by free bits (stale entries skipped)
+        for (int pos = 0; pos < C; ++pos) {
+            const int c = order[pos];
+            const int k = coff[c + 1] - coff[c];
+            int ws = -1;
+            for (int f = k; f <= 64 && ws < 0; ++f) {
+                auto& lst = by_free[f];
+                while (!lst.empty() && ws < 0) {
+                    const int wi = lst.back();
+                    lst.pop_back();
+                    if (64 - used[wi] == f && (int)words[wi].size() < kWordMembers) ws = wi;
+                }
+            }
+            if (ws < 0) {
+                ws = (int)words.size();
+                words.emplace_back();
+                used.push_back(0);
+            }
+            words[ws].push_back({c, used[ws]});
+            used[ws] += k;
+            if (used[ws] < 64 && (int)words[ws].size() < kWordMembers) by_free[64 - used[ws]].push_back(ws);
+        }
+        if ((int)words.size() < C) {
+            word_first.push_back(0);
+            for (size_t wi = 0; wi < words.size(); ++wi) {
+                for (const auto& m : words[wi]) wmem.push_back(m);
+                word_first.push_back((int)wmem.size());
+                word_bits.push_back(used[wi]);
+            }
+            nwaves = ((int)words.size() + P - 1) / P;
+        }
+    }
+    // round records: fused waves and packed waves write their outputs from them
+    int hcap = 0;
+    if (fused || !word_first.empty()) {
+        rc = stage_rounds(g, tune, P, &hcap);
+        if (rc) return rc;
+        if (hcap == 0 && !word_first.empty()) {  // no room for records: one cluster per word
+            word_first.clear();
+            wmem.clear();
+            word_bits.clear();
+            nwaves = (C + P - 1) / P;
+        }
+    }
+    const bool packed = !word_first.empty();
+    const int NW = packed ? (int)word_bits.size() : C;  // slot words of the call
     const int64_t stage_dist_bytes = (G * wave_dist + 255) / 256 * 256;
     if (staged) {
         rc = ensure_dev(&g->stage, &g->stage_cap, stage_dist_bytes + 8 * G * wave_masks);
@@ -1932,21 +2179,63 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     };
     // Captured graphs hold these device pointers: when one of them moves, every
     // cached graph goes (a replay would read the freed buffer).
-    const void* held[2] = {g->slots, g->seeds};
+    const void* held[4] = {g->slots, g->seeds, g->members, g->bitm};
     cbfs_graph_s::Upload& up = g->up[g->calls % cbfs_graph_s::kUploadRing];
     if (up.done) CK(cudaEventSynchronize(up.done));  // this entry's previous upload has been read
     rc = ensure_dev(&g->slots, &g->slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_pinned(&up.slots, &up.slots_cap, (int64_t)nwaves * P);
     if (!rc) rc = ensure_dev(&g->seeds, &g->seeds_cap, total_src);
     if (!rc) rc = ensure_pinned(&up.seeds, &up.seeds_cap, total_src);
-    if (held[0] != (const void*)g->slots || held[1] != (const void*)g->seeds) drop_graphs(g);
+    if (!rc && packed) rc = ensure_dev(&g->members, &g->members_cap, C);
+    if (!rc && packed) rc = ensure_pinned(&up.members, &up.members_cap, C);
+    if (!rc && packed) rc = ensure_dev(&g->bitm, &g->bitm_cap, (int64_t)nwaves * P * 64);
+    if (!rc && packed) rc = ensure_pinned(&up.bitm, &up.bitm_cap, (int64_t)nwaves * P * 64);
+    if (held[0] != (const void*)g->slots || held[1] != (const void*)g->seeds || held[2] != (const void*)g->members ||
+        held[3] != (const void*)g->bitm)
+        drop_graphs(g);
     if (rc) return rc;
     if (!up.done) CK(cudaEventCreateWithFlags(&up.done, cudaEventDisableTiming));
     g->calls += 1;
     // slot tables and seeds of every wave, staged once
     std::vector<int64_t> wave_seed_off(nwaves + 1, 0);
     int64_t ns = 0;
-    for (int wv = 0; wv < nwaves; ++wv) {
+    // packed: each word's members (its first member's wave-local index in
+    // SlotDesc.cluster, their count in .pad), the bit table, and the seeds with
+    // their member index
+    for (int wv = 0; packed && wv < nwaves; ++wv) {
+        wave_seed_off[wv] = ns;
+        const int m0 = word_first[(size_t)wv * P];
+        uint8_t* bt = up.bitm + (size_t)wv * P * 64;
+        memset(bt, 0xFF, (size_t)P * 64);
+        for (int s = 0; s < P; ++s) {
+            const int pos = wv * P + s;
+            SlotDesc sd;
+            memset(&sd, 0, sizeof(sd));
+            if (pos < NW) {
+                sd.cluster = word_first[pos] - m0;
+                sd.pad = word_first[pos + 1] - word_first[pos];
+                for (int mi = word_first[pos]; mi < word_first[pos + 1]; ++mi) {
+                    const int c = wmem[mi].first, off = wmem[mi].second;
+                    const int k = coff[c + 1] - coff[c];
+                    MemberDesc md;
+                    memset(&md, 0, sizeof(md));
+                    md.dist = dist + (size_t)c * (size_t)n;
+                    md.masks = d ? masks + (size_t)c * (size_t)d * (size_t)n : nullptr;
+                    md.mask = ((k >= 64) ? ~0ull : ((1ull << k) - 1ull)) << off;
+                    md.off = off;
+                    md.word = s;
+                    up.members[mi] = md;
+                    sd.all |= md.mask;
+                    for (int b = off; b < off + k; ++b) bt[s * 64 + b] = (uint8_t)(mi - m0);
+                    for (int j = 0; j < k; ++j)
+                        up.seeds[ns++] = ((uint64_t)(mi - m0) << 48) | ((uint64_t)s << 40) | ((uint64_t)(off + j) << 32) |
+                                         (uint32_t)src[coff[c] + j];
+                }
+            }
+            up.slots[(size_t)wv * P + s] = sd;
+        }
+    }
+    for (int wv = 0; !packed && wv < nwaves; ++wv) {
         wave_seed_off[wv] = ns;
         for (int s = 0; s < P; ++s) {
             const int pos = wv * P + s;
@@ -1974,6 +2263,10 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     CK(cudaMemcpyAsync(g->slots, up.slots, sizeof(SlotDesc) * (size_t)nwaves * P, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(g->seeds, up.seeds, sizeof(uint64_t) * (size_t)std::max<int64_t>(ns, 1),
                        cudaMemcpyHostToDevice, st));
+    if (packed) {
+        CK(cudaMemcpyAsync(g->members, up.members, sizeof(MemberDesc) * (size_t)C, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(g->bitm, up.bitm, (size_t)nwaves * P * 64, cudaMemcpyHostToDevice, st));
+    }
     CK(cudaEventRecord(up.done, st));
     CK(map_seeds(g->seeds, ns, g->iperm_d, st));
     // The status word is sticky: it is not cleared here, so an error of an
@@ -2029,20 +2322,28 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     w.masks_r = g->masks_r;
     w.dense_div = dense_div;
     w.grid_a = g->grid_a[pi];
-    w.fused_pull = (tune && tune->fused_pull > 0) ? 1 : 0;
-    if (w.fused_pull) {
+    w.fused_pull = fused ? 1 : 0;
+    if (fused || packed) {
         // no internal rows: the vertex phase (in the pull or in phase A) records each
-        // round's new sources (round records, then k_flush) or, past the records or
-        // without them, writes the slots' outputs directly (cleared per wave by
-        // k_clear_outputs); no emit
+        // round's new sources (round records, then k_flush / k_flush_packed) or, past
+        // the records or without them, writes the outputs directly (cleared per wave
+        // by k_clear_outputs when there are no records); no emit
         w.dist_r = nullptr;
         w.masks_r = nullptr;
         w.wmask_r = nullptr;
-        rc = stage_rounds(g, tune, P, &w.hcap);
-        if (rc) return rc;
+        w.hcap = hcap;
         w.hist = g->hist;
         w.fbh = g->fbh;
     }
+    // packed: the wave's members and bit table (per wave, set below)
+    auto set_members = [&](Wave& x, int wv) {
+        if (!packed) return;
+        const int m0 = word_first[(size_t)wv * P];
+        const int m1 = word_first[(size_t)std::min(NW, (wv + 1) * P)];
+        x.members = g->members + m0;
+        x.nmembers = m1 - m0;
+        x.bit_member = g->bitm + (size_t)wv * P * 64;
+    };
 
     // Graph mode (device outputs): the call runs as one cached CUDA graph per
     // call shape whose rounds loop on the device, and is stream-ordered: the
@@ -2061,9 +2362,10 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
         std::vector<Wave> waves((size_t)nwaves, wg);
         uint64_t key = 1469598103934665603ull;
         for (int wv = 0; wv < nwaves; ++wv) {
-            waves[wv].nslots = std::min(P, C - wv * P);
+            waves[wv].nslots = std::min(P, NW - wv * P);
             waves[wv].alpha = wave_alpha(wv);
             waves[wv].slots = g->slots + (size_t)wv * P;
+            set_members(waves[wv], wv);
             key = fnv1a(key, &waves[wv], sizeof(Wave));
         }
         key = fnv1a(key, wave_seed_off.data(), sizeof(int64_t) * wave_seed_off.size());
@@ -2116,9 +2418,10 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     CK(cudaMemsetAsync(g->wave_flags, 0, sizeof(int) * (size_t)nwaves, st));
     auto run_wave = [&](int wv, int bound, bool rerun, int* rounds_out) -> int {
         const int c0 = wv * P;
-        w.nslots = std::min(P, C - c0);
+        w.nslots = std::min(P, NW - c0);
         w.alpha = wave_alpha(wv);
         w.slots = g->slots + (size_t)wv * P;
+        set_members(w, wv);
         CK(cudaMemsetAsync(g->vis, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         CK(cudaMemsetAsync(g->acc, 0, sizeof(uint64_t) * (size_t)P * (size_t)n, st));
         if (w.fused_pull && !w.hcap)  // a fused pull round may read any vertex's entry
@@ -2453,6 +2756,8 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     dev_free(g->status);
     dev_free(g->slots);
     dev_free(g->seeds);
+    dev_free(g->members);
+    dev_free(g->bitm);
     for (cudaEvent_t e : g->events) cudaEventDestroy(e);
     drop_graphs(g);
     dev_free(g->stage);
@@ -2468,6 +2773,8 @@ int cbfs_graph_destroy(cbfs_graph_t g) {
     for (auto& u : g->up) {
         if (u.slots) cudaFreeHost(u.slots);
         if (u.seeds) cudaFreeHost(u.seeds);
+        if (u.members) cudaFreeHost(u.members);
+        if (u.bitm) cudaFreeHost(u.bitm);
         if (u.done) cudaEventDestroy(u.done);
     }
     delete g;

@@ -45,6 +45,17 @@ struct SlotDesc {
     int32_t pad;
 };
 
+// A cluster packed into a slot word with others (packed waves): its sources
+// are bits [off, off + k) of word `word`; its outputs are dist / masks.
+struct MemberDesc {
+    uint8_t* dist;
+    uint64_t* masks;
+    uint64_t mask;  // its bits in the word: ((1 << k) - 1) << off
+    int32_t off;
+    int32_t word;
+};
+constexpr int kWordMembers = 31;  // clusters per slot word at most (a wave's members fit a byte index)
+
 // Per-round control block, zeroed at the start of every wave.
 struct RoundCtl {
     unsigned long long qlen;   // queue entries (vertices) of F_i, appended during round i-1
@@ -126,6 +137,9 @@ struct Wave {
                             // the sources new at u in round i, valid iff bit u of fbh[i] is set
     uint32_t* fbh;          // [hcap][bitmap words] F_i's bitmap, copied by phase A of round i
     int hcap;               // rounds recorded (0: none, outputs written directly as they arise)
+    const MemberDesc* members;  // packed waves: the clusters of the wave, word by word
+    const uint8_t* bit_member;  // [P][64] member of each bit of each word (0xFF: none)
+    int nmembers;           // 0: one cluster per slot word (the slot's own outputs)
     int dense_div;          // the vertex phase scans every vertex when qlen * dense_div > n
     int grid_a;             // CTAs of the vertex phase (0: the edge phase's grid)
     int fused_pull;         // 1: pull rounds do their vertices' vertex phase on the spot
@@ -152,7 +166,9 @@ inline ScratchSizes scratch_sizes(int64_t n, int P) {
 
 __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(status, 0, code); }
 
-// Traversal kernels (cbfs_core.cu).  seeds[i] = slot << 40 | j << 32 | vertex.
+// Traversal kernels (cbfs_core.cu).  seeds[i] = member << 48 | slot << 40 |
+// j << 32 | vertex (j: the source's bit in the slot word; member: the index
+// of its cluster in a packed wave's member table).
 __global__ void k_seed(Wave w, const uint64_t* seeds, int count);
 __global__ void k_check_sources(Wave w, const uint64_t* seeds, int count, int bound_round, int* unfinished);
 template <int P>
@@ -167,6 +183,9 @@ __global__ void k_emit(Wave w, const int32_t* iperm);
 // outputs directly), else after the wave when it ended before that round.
 template <int P>
 __global__ void k_flush(Wave w, const int32_t* iperm, int round, int at_cap, int bound_round);
+// The same for packed waves (nmembers > 0): each member's outputs from its bits.
+template <int P>
+__global__ void k_flush_packed(Wave w, const int32_t* iperm, int round, int at_cap, int bound_round);
 
 // Internal vertex order (cbfs_relabel.cu), computed on the device: ranks by
 // degree, highest first, ties to the smaller id; perm[rank] = id,

@@ -140,6 +140,55 @@ def test_fused_round_records_at_every_cap(cb, stage_rounds):
                     assert (cb.as_numpy_u64(bm[c]) == om).all(), (graph, t, rep, c)
 
 
+@pytest.mark.parametrize("tune", [{"slots": 4}, {"slots": 2, "host_loop": 1}, {"slots": 4, "stage_rounds": 2},
+                                  {"slots": 4, "fused_pull": 1}, dict(PULL_EAGER, slots=8),
+                                  {"slots": 1, "stage_rounds": 3, "host_loop": 1}])
+def test_packed_waves_equal_oracle(cb, tune):
+    """Clusters that fill only part of a 64-bit word share words (packed
+    waves): 70 clusters of 1..64 sources (many small, some sharing source
+    vertices), each compared with the oracle; the same call without packing
+    gives the same outputs.  stage_rounds 2 / 3: the words' outputs come from
+    two or three rounds of records and directly, member by member, after."""
+    off, adj = I.rmat(12, seed=31)
+    g = cb.Graph(off, adj)
+    stars, d = I.star_clusters(off, adj, 60, seed=12, size="uniform")
+    clusters = list(stars) + [stars[3][: max(1, len(stars[3]) // 2)], stars[5], stars[7][:1]] * 3
+    clusters.append(np.array([int(np.argmax(np.diff(off)))], np.int32))
+    want = [O.cbfs_alg1(off, adj, S, d) for S in clusters]
+    for rep in range(2):
+        bd, bm = g.run_batched(clusters, d, tune=tune)
+        for c, (od, om) in enumerate(want):
+            assert (bd[c].cpu().numpy() == od).all(), (tune, rep, c)
+            assert (cb.as_numpy_u64(bm[c]) == om).all(), (tune, rep, c)
+    ud, um = g.run_batched(clusters, d, tune=dict(tune, pack=-1))
+    assert torch.equal(ud, bd) and torch.equal(um, bm)
+
+
+def test_packed_single_sources_and_errors(cb):
+    """64 single-source clusters at d = 0 (31 to a word), then 0-diameter
+    clusters packed with one whose sources are 4 apart at d = 2: the call
+    reports CBFS_E_DIAMETER, and the handle's next call is exact."""
+    off, adj = I.rmat(11, seed=33)
+    g = cb.Graph(off, adj)
+    deg = np.diff(off)
+    singles = [np.array([v], np.int32) for v in np.flatnonzero(deg > 0)[:64]]
+    bd, bm = g.run_batched(singles, 0, tune={"slots": 2})
+    for c, S in enumerate(singles):
+        od, _ = O.cbfs_alg1(off, adj, S, 0)
+        assert (bd[c].cpu().numpy() == od).all(), c
+    poff, padj = I.path(60)
+    gp = cb.Graph(poff, padj)
+    bad = [np.array([v], np.int32) for v in range(10)] + [np.array([20, 24], np.int32)]
+    with pytest.raises(cb.CbfsError) as e:
+        gp.run_batched(bad, 2, tune={"slots": 2})
+    assert e.value.code == cb.E_DIAMETER
+    ok = [np.array([v], np.int32) for v in range(10)] + [np.array([20, 22], np.int32)]
+    bd, bm = gp.run_batched(ok, 2, tune={"slots": 2})
+    for c, S in enumerate(ok):
+        od, om = O.cbfs_alg1(poff, padj, S, 2)
+        assert (bd[c].cpu().numpy() == od).all() and (cb.as_numpy_u64(bm[c]) == om).all(), c
+
+
 def test_waves_grouped_by_size_or_in_call_order(cb):
     """Clusters of mixed sizes: the default groups them into waves by size,
     wave_order = 1 keeps the call order; both, host-driven and replayed,
