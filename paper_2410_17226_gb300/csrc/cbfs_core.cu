@@ -1143,9 +1143,11 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 2 : 4)) k_flush(Wave w, co
 // member come from the same round records, masked to the member's bits and
 // shifted down to its own bit order: Delta is the first recorded round with
 // bits of the member new at u, S_v[i] the member's bits of the record of
-// round Delta + i.  Word by word, a thread keeps each member's Delta and
-// written-word mask in shared memory; the bits of a record are taken member
-// by member (the member of a bit comes from the wave's bit table).
+// round Delta + i.  Word by word, in two passes: the first walks v's
+// records and keeps each member's Delta in shared memory (the member of a bit
+// comes from the wave's bit table); the second writes member by member and
+// subset by subset, every lane of a warp at once, so that a warp's stores
+// fill whole sectors of an output row.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_flush_packed(Wave w, const int32_t* iperm, int round, int at_cap,
                                                             int bound_round) {
@@ -1153,7 +1155,6 @@ __global__ void __launch_bounds__(kThreads) k_flush_packed(Wave w, const int32_t
     __shared__ MemberDesc sm[P * kWordMembers];
     __shared__ uint8_t sbit[P * 64];
     __shared__ uint8_t sdl[kWordMembers][kThreads];
-    __shared__ uint16_t swm[kWordMembers][kThreads];
     __shared__ int s_first[P + 1];
     __shared__ int s_rounds;
     if (w.round_dev) round = *w.round_dev;
@@ -1204,10 +1205,9 @@ __global__ void __launch_bounds__(kThreads) k_flush_packed(Wave w, const int32_t
         }
         for (int s = 0; s < w.nslots; ++s) {
             const int m0 = s_first[s], mc = s_first[s + 1] - m0;
-            for (int i = 0; i < mc; ++i) {
-                sdl[i][t] = 0xFF;
-                swm[i][t] = 0;
-            }
+            for (int i = 0; i < mc; ++i) sdl[i][t] = 0xFF;
+            // pass 1: each member's Delta (its first recorded round), and any member
+            // bits arriving more than d rounds after it (CBFS_E_DIAMETER)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 uint64_t m = mk[b];
@@ -1232,31 +1232,27 @@ __global__ void __launch_bounds__(kThreads) k_flush_packed(Wave w, const int32_t
                                 set_status(w.status, CBFS_E_INVALID);
                                 break;
                             }
-                            const MemberDesc& M = sm[m0 + i];
-                            left &= ~(M.mask | (1ull << bt));  // bit bt always goes: the loop ends
-                            const uint64_t bits = (x[k] & M.mask) >> M.off;
-                            int dl = sdl[i][t];
-                            if (dl == 0xFF) {
-                                dl = rr[k];
-                                sdl[i][t] = (uint8_t)dl;
-                            }
-                            const int j = rr[k] - dl;
-                            if (j < d) {
-                                M.masks[(size_t)j * (size_t)n + v] = bits;
-                                swm[i][t] = (uint16_t)(swm[i][t] | (1u << j));
-                            } else if (j > d) {
-                                set_status(w.status, CBFS_E_DIAMETER);
-                            }
+                            left &= ~(sm[m0 + i].mask | (1ull << bt));  // bit bt always goes: the loop ends
+                            const int dl = sdl[i][t];
+                            if (dl == 0xFF) sdl[i][t] = (uint8_t)rr[k];
+                            else if (rr[k] - dl > d) set_status(w.status, CBFS_E_DIAMETER);
                         }
                     }
                 }
             }
+            // pass 2: member by member and subset by subset, every lane at once
+            // (consecutive callers' words of one output row), each word written once
             for (int i = 0; i < mc; ++i) {
                 const MemberDesc& M = sm[m0 + i];
-                M.dist[v] = sdl[i][t];
-                const uint32_t wm = swm[i][t];
-                for (int j = 0; j < d; ++j)
-                    if (!((wm >> j) & 1u)) M.masks[(size_t)j * (size_t)n + v] = 0ull;
+                const int dl = sdl[i][t];
+                M.dist[v] = (uint8_t)dl;
+                for (int j = 0; j < d; ++j) {
+                    const int r = dl + j;  // dl == 0xFF: never reached, r > 254 >= R
+                    uint64_t x = 0;
+                    if (r < R && ((mk[r >> 6] >> (r & 63)) & 1ull))
+                        x = w.hist[((size_t)r * (size_t)n + u) * P + s];
+                    M.masks[(size_t)j * (size_t)n + v] = (x & M.mask) >> M.off;
+                }
             }
         }
     }
