@@ -1054,12 +1054,13 @@ def record_traffic(csv_paths: str, run_json: str, note: str):
     return 0
 
 
-def memset_bytes_per_wave(n: int, P: int) -> int:
+def memset_bytes_per_wave(n: int, P: int, rows: bool = True) -> int:
     """Bytes the per-wave state resets write: vis and acc (8 P bytes per
-    vertex each), the claim stamps (4), the Delta rows (P), two frontier
-    bitmaps and the round control blocks (288 x 56 bytes)."""
+    vertex each), the claim stamps (4), the Delta rows (P; waves with round
+    records have none), two frontier bitmaps and the round control blocks
+    (288 x 56 bytes)."""
     bitmap_words = (n + 31) // 32 + 1
-    return (16 * P + 4 + P) * n + 2 * 4 * bitmap_words + 288 * 56
+    return (16 * P + 4 + (P if rows else 0)) * n + 2 * 4 * bitmap_words + 288 * 56
 
 
 def traffic_from_csv(csv_paths, run: dict, note: str) -> dict:
@@ -1071,7 +1072,7 @@ def traffic_from_csv(csv_paths, run: dict, note: str) -> dict:
     bench multiplies its own launch's algorithmic bytes by this ratio."""
     import csv as csv_
 
-    kinds = ("k_seed", "k_phase_a", "k_phase_b", "k_emit", "k_check_sources", "k_map_seeds")
+    kinds = ("k_seed", "k_phase_a", "k_phase_b", "k_emit", "k_flush", "k_check_sources", "k_map_seeds")
     per_kernel, launches = {}, {}
     for path in csv_paths:
         with open(path) as f:
@@ -1094,13 +1095,17 @@ def traffic_from_csv(csv_paths, run: dict, note: str) -> dict:
             launches.setdefault(key, set()).add((path, rec["ID"]))
     n, d, C = int(run["n"]), int(run["d"]), int(run["clusters"])
     P = int(run["tune"]["slots"])
-    waves = (C + P - 1) // P
+    # k_seed runs once per wave (packed waves hold more clusters than slots);
+    # waves that write their outputs from round records (k_flush) have no rows
+    seeds = [k for k in launches if "k_seed" in k]
+    waves = len(launches[seeds[0]]) if seeds else (C + P - 1) // P
+    rows = not any("k_flush" in k for k in per_kernel)
     kernel_bytes = sum(per_kernel.values())
-    memsets = waves * memset_bytes_per_wave(n, P)
+    memsets = waves * memset_bytes_per_wave(n, P, rows)
     alg = ARC_BYTES * int(run["A"]) + VERTEX_BYTES * int(run["V"]) + C * n * (1 + 8 * d)
     return {"traversal": {"dram_bytes_per_alg_byte": (kernel_bytes + memsets) / alg,
                           "kernel_dram_bytes": int(kernel_bytes), "memset_bytes": int(memsets),
-                          "alg_bytes": int(alg), "clusters": C, "slots": P,
+                          "alg_bytes": int(alg), "clusters": C, "slots": P, "waves": waves,
                           "per_kernel_bytes": {k: int(v) for k, v in sorted(per_kernel.items())},
                           "launches_captured": {k: len(v) for k, v in sorted(launches.items())},
                           "source_hash": kernel_source_hash(), "measured_on": note}}

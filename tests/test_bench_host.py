@@ -80,3 +80,22 @@ def test_lockstep_rounds_counts_idle_slot_rounds():
     assert out["waves"] == 2 and out["wave_rounds"] == 8 + 6
     assert out["cluster_rounds"] == 20
     assert out["busy_slot_round_share"] == round(20 / (2 * 8 + 2 * 6), 4)
+
+
+def test_traffic_of_packed_waves_counts_waves_from_seed_launches(tmp_path):
+    """A call whose waves write their outputs from round records (k_flush)
+    and hold more clusters than slots: waves = k_seed launches, no Delta-row
+    memsets."""
+    p = tmp_path / "c.csv"
+    _write_csv(p, [
+        ["0", "cbfs::k_seed(cbfs::Wave, const unsigned long *, int)", "dram__bytes_read.sum", "byte", "100"],
+        ["1", "cbfs::k_seed(cbfs::Wave, const unsigned long *, int)", "dram__bytes_read.sum", "byte", "100"],
+        ["2", "void cbfs::k_flush_packed<4>(cbfs::Wave, const int *, int, int, int)", "dram__bytes_write.sum",
+         "Mbyte", "7"],
+    ])
+    run = {"n": 1000, "d": 2, "clusters": 24, "A": 10_000_000, "V": 100_000, "tune": {"slots": 4}}
+    out = bench.traffic_from_csv([str(p)], run, "test")["traversal"]
+    assert out["waves"] == 2
+    assert out["memset_bytes"] == 2 * bench.memset_bytes_per_wave(1000, 4, rows=False)
+    assert out["memset_bytes"] == 2 * ((16 * 4 + 4) * 1000 + 2 * 4 * 33 + 288 * 56)
+    assert out["per_kernel_bytes"]["cbfs::k_flush_packed<4>"] == int(7e6)
