@@ -464,7 +464,7 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
         dist = torch.empty((per_launch, n), dtype=torch.uint8, device="cuda")
         masks = torch.empty((per_launch, d, n), dtype=torch.int64, device="cuda")
         total_ms, A, V, src_edges, rounds = 0.0, 0, 0, 0, 0
-        lock = {"waves": 0, "wave_rounds": 0, "cluster_rounds": 0}
+        lock = {"waves": 0, "words": 0, "wave_rounds": 0, "word_rounds": 0, "cluster_rounds": 0}
         for b in range(0, count, per_launch):
             part = clusters[b:b + per_launch]
             k = len(part)
@@ -489,7 +489,7 @@ def road_grid_throughput(cbfs, seed: int, side: int = 4096, count: int = 64, per
             "ms_all_clusters": round(total_ms, 2),
             "gteps": round(src_edges / (total_ms / 1e3) / 1e9, 2), "max_rounds": rounds,
             "lockstep": dict(lock, busy_slot_round_share=round(
-                lock["cluster_rounds"] / max(lock["wave_rounds"] * max(int(tset["slots"]), 1), 1), 4)),
+                lock["word_rounds"] / max(lock["wave_rounds"] * max(int(tset["slots"]), 1), 1), 4)),
             "arcs_per_s": round(A / (total_ms / 1e3), 1),
             "alg_gbs": round(alg / (total_ms / 1e3) / 1e9, 1), "alg_frac": round(alg / (total_ms / 1e3) / 1e9 / peak, 4)}
 
@@ -888,21 +888,21 @@ def run_cbfs(args, ws, rank, local):
         nxt["ll_quality"] = ll_quality(cbfs, g, off, adj, seed=rank_seed(rank) + 24)
         nxt["road_grid"] = road_grid_throughput(cbfs, seed=I.MASTER_SEED + 3)
 
-    # End to end through the public API: the CSR from page-locked host memory
-    # (H2D inside graph create), the batched traversal writing the label store
-    # on the device, the query with its pairs H2D and its answers D2H -- the
-    # answers are the step's result.  A second variant also streams all 18 GB
-    # of dist/masks into page-locked host memory during the traversal; its
-    # rate depends on the machine's host-memory bandwidth (shared with the
-    # other GPUs' tenants here), so it is reported beside the headline.
+    # End to end through the public API, the timed step's work: the CSR from
+    # page-locked host memory (H2D inside graph create), the batched traversal
+    # into device outputs, the label append, the query with its pairs H2D and
+    # its answers D2H -- the answers are the step's result.  Two variants
+    # beside it: the traversal writing the label store itself
+    # (cbfs_run_batched_labels, no outputs kept; label calls keep one cluster
+    # per slot word), and that plus all 18 GB of dist/masks streamed into
+    # page-locked host memory during the traversal, whose rate depends on the
+    # machine's host-memory bandwidth (shared with the other GPUs' tenants).
     e2e = None
     if args.e2e_steps > 0:
         off_pin, adj_pin, dist_h, masks_h = e2e_host
         bi = off.nbytes + adj.nbytes + src_cat.nbytes + coff.nbytes + pairs.nbytes
-        del dist, masks
-        torch.cuda.empty_cache()
 
-        def e2e_run(host_outputs: bool):
+        def e2e_run(mode: str):
             times, parts = [], []
             for it in range(args.e2e_steps + 1):  # the first step is an untimed warm-up
                 torch.cuda.synchronize()
@@ -910,9 +910,13 @@ def run_cbfs(args, ws, rank, local):
                 g2 = cbfs.Graph(off_pin, adj_pin, validate=True)
                 t1 = time.perf_counter()
                 L.reset()
-                g2.run_batched_labels(None, d, L, dist=dist_h if host_outputs else None,
-                                      masks=masks_h if host_outputs else None, tune=tset, sources_concat=src_cat,
-                                      cluster_off=coff)
+                if mode == "outputs":
+                    g2.run_batched(None, d, dist, masks, tune=tset, sources_concat=src_cat, cluster_off=coff)
+                    L.append(dist, masks, ks)
+                else:
+                    g2.run_batched_labels(None, d, L, dist=dist_h if mode == "host" else None,
+                                          masks=masks_h if mode == "host" else None, tune=tset,
+                                          sources_concat=src_cat, cluster_off=coff)
                 t2 = time.perf_counter()
                 pairs_dev.copy_(pin_pairs, non_blocking=True)
                 L.query(pairs_dev, out=answers)
@@ -927,15 +931,23 @@ def run_cbfs(args, ws, rank, local):
             return t, dict(zip(("graph_create", "traversal_labels", "query"),
                                [round(1e3 * statistics.median(p[i] for p in parts), 2) for i in range(3)]))
 
-        e_t, e_parts = e2e_run(False)
+        e_t, e_parts = e2e_run("outputs")
         e2e = {"value": round(src_edges / e_t / 1e9 * ws, 4), "unit": "GTEPS", "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(args.query_batch * 2), "ms_per_step": round(e_t * 1e3, 3),
                "includes": "graph create + validate from the page-locked host CSR; batched C-BFS of all clusters "
-                           "writing the label store on the device (cbfs_run_batched_labels); query with pairs H2D "
+                           "into device outputs (cbfs_run_batched) and the label append; query with pairs H2D "
                            "and answers D2H",
                "ms_parts": e_parts}
+        l_t, l_parts = e2e_run("labels")
+        e2e["labels_by_the_traversal"] = {
+            "value": round(src_edges / l_t / 1e9 * ws, 4), "unit": "GTEPS", "ms_per_step": round(l_t * 1e3, 3),
+            "ms_parts": l_parts,
+            "includes": "the same with the traversal writing the label store itself (cbfs_run_batched_labels, "
+                        "no outputs kept)"}
+        del dist, masks
+        torch.cuda.empty_cache()
         if dist_h is not None:
-            h_t, h_parts = e2e_run(True)
+            h_t, h_parts = e2e_run("host")
             e2e["with_host_outputs"] = {
                 "value": round(src_edges / h_t / 1e9 * ws, 4), "unit": "GTEPS", "ms_per_step": round(h_t * 1e3, 3),
                 "d2h_bytes_per_step": int(dist_h.numel() + masks_h.numel() * 8 + args.query_batch * 2),
@@ -983,20 +995,54 @@ def run_cbfs(args, ws, rank, local):
     return 0
 
 
+def pack_words(ks, per_word: int = 31) -> list:
+    """The library's slot words for a call with device outputs (cbfs_tune_t
+    pack): clusters by size descending (ties in call order), each into the
+    fullest word with room for it (the latest such word first), at most
+    `per_word` to a word, 64 bits each; one cluster per word when that saves
+    no words.  Reporting only: the library decides on its own."""
+    ks = [int(k) for k in ks]
+    order = sorted(range(len(ks)), key=lambda c: -ks[c])
+    words, used, by_free = [], [], [[] for _ in range(65)]
+    for c in order:
+        k, ws = ks[c], -1
+        for f in range(k, 65):
+            lst = by_free[f]
+            while lst and ws < 0:
+                wi = lst.pop()
+                if 64 - used[wi] == f and len(words[wi]) < per_word:
+                    ws = wi
+            if ws >= 0:
+                break
+        if ws < 0:
+            ws = len(words)
+            words.append([])
+            used.append(0)
+        words[ws].append(c)
+        used[ws] += k
+        if used[ws] < 64 and len(words[ws]) < per_word:
+            by_free[64 - used[ws]].append(ws)
+    if len(ks) < 2 or len(words) >= len(ks):
+        return [[c] for c in order]
+    return words
+
+
 def lockstep_rounds(ks, rounds, slots: int) -> dict:
-    """How long clusters wait for each other in the lockstep waves: the
-    library groups a call's clusters into waves of `slots` by size (sizes
-    descending, ties in call order), and a wave runs as many rounds as its
-    deepest cluster.  Returns the rounds the waves ran against the rounds
-    their clusters needed (slot-rounds), so 1 - ratio is the idle share."""
-    ks = np.asarray(ks)
+    """How long work waits in the lockstep waves: the library packs a call's
+    clusters into 64-bit slot words (pack_words), `slots` words to a wave in
+    that order, and a word runs as many rounds as its deepest cluster, a wave
+    as many as its deepest word.  Returns the rounds the waves ran against
+    the rounds their words needed (slot-rounds; 1 - ratio is the idle share)
+    and the rounds the clusters needed."""
     rounds = np.asarray(rounds, dtype=np.int64)
-    order = np.argsort(-ks, kind="stable")
+    words = pack_words(ks)
+    word_rounds = [int(rounds[w].max()) for w in words]
     P = max(1, int(slots))
-    wave_rounds = [int(rounds[order[i:i + P]].max()) for i in range(0, len(order), P)]
-    used = int(rounds.sum())
-    offered = sum(r * min(P, len(order) - i * P) for i, r in enumerate(wave_rounds))
-    return {"waves": len(wave_rounds), "wave_rounds": int(sum(wave_rounds)), "cluster_rounds": used,
+    wave_rounds = [max(word_rounds[i:i + P]) for i in range(0, len(words), P)]
+    used = sum(word_rounds)
+    offered = sum(r * min(P, len(words) - i * P) for i, r in enumerate(wave_rounds))
+    return {"waves": len(wave_rounds), "words": len(words), "wave_rounds": int(sum(wave_rounds)),
+            "word_rounds": int(used), "cluster_rounds": int(rounds.sum()),
             "busy_slot_round_share": round(used / max(offered, 1), 4)}
 
 

@@ -77,9 +77,25 @@ def test_lockstep_rounds_counts_idle_slot_rounds():
     ks = [5, 3, 9, 1]
     rounds = [4, 6, 8, 2]
     out = bench.lockstep_rounds(ks, rounds, 2)
-    assert out["waves"] == 2 and out["wave_rounds"] == 8 + 6
-    assert out["cluster_rounds"] == 20
-    assert out["busy_slot_round_share"] == round(20 / (2 * 8 + 2 * 6), 4)
+    # 5 + 3 + 9 + 1 bits pack into one word: one wave of one word, 8 rounds
+    assert out["words"] == 1 and out["waves"] == 1 and out["wave_rounds"] == 8
+    assert out["cluster_rounds"] == 20 and out["busy_slot_round_share"] == 1.0
+    # 64-source clusters take a word each: equal sizes keep call order, waves (0, 1) and (2, 3)
+    big = [64] * 4
+    out = bench.lockstep_rounds(big, rounds, 2)
+    assert out["words"] == 4 and out["waves"] == 2 and out["wave_rounds"] == 6 + 8
+    assert out["busy_slot_round_share"] == round(20 / (2 * 6 + 2 * 8), 4)
+
+
+def test_pack_words_best_fit_largest_first():
+    """Sizes 40, 30, 20, 10, 5, 64: 64 alone; 40 + 20 (best fit for 20: the
+    word with 24 free) ; 30 + 10 + 5 ... and at most 31 clusters to a word."""
+    words = bench.pack_words([40, 30, 20, 10, 5, 64])
+    sizes = sorted(sorted([40, 30, 20, 10, 5, 64][c] for c in w) for w in words)
+    assert sizes == [[5, 10, 30], [20, 40], [64]]
+    ones = bench.pack_words([1] * 70)
+    assert [len(w) for w in ones] == [31, 31, 8]
+    assert bench.pack_words([64, 64]) == [[0], [1]]
 
 
 def test_traffic_of_packed_waves_counts_waves_from_seed_launches(tmp_path):
