@@ -299,8 +299,9 @@ def bfs_comparison(g, off, adj, seed: int, seq=None):
     for S in clusters:
         singles = [np.array([s], np.int32) for s in S]
         cb_ms.append(timed_ms(lambda: g.run_batched([S], d, tune={"slots": 1})))
-        bfs_ms.append(timed_ms(lambda: g.run_batched(singles, 0, tune={"slots": 1})))
-        bfs8_ms.append(timed_ms(lambda: g.run_batched(singles, 0, tune={"slots": 8})))
+        # separate BFSs: one source per slot word (packing would make them one C-BFS)
+        bfs_ms.append(timed_ms(lambda: g.run_batched(singles, 0, tune={"slots": 1, "pack": -1})))
+        bfs8_ms.append(timed_ms(lambda: g.run_batched(singles, 0, tune={"slots": 8, "pack": -1})))
     # undirected edges of the reached component (the same for every source of a cluster)
     hd, _ = g.run([int(clusters[0][0])], 0)
     comp_edges = int(deg[hd.cpu().numpy() != 255].sum()) // 2
@@ -917,6 +918,7 @@ def run_cbfs(args, ws, rank, local):
                     g2.run_batched_labels(None, d, L, dist=dist_h if mode == "host" else None,
                                           masks=masks_h if mode == "host" else None, tune=tset,
                                           sources_concat=src_cat, cluster_off=coff)
+                torch.cuda.synchronize()  # the traversal's share of the step (the calls only enqueue)
                 t2 = time.perf_counter()
                 pairs_dev.copy_(pin_pairs, non_blocking=True)
                 L.query(pairs_dev, out=answers)
