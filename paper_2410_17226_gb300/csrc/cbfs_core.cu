@@ -1093,8 +1093,7 @@ __global__ void __launch_bounds__(kThreads, (P >= 8 ? 2 : 4)) k_flush(Wave w, co
             const int nb = R - b0 < 64 ? R - b0 : 64;
             uint64_t m = 0;
 #pragma unroll 8
-            for (int k = 0; k < 64; ++k)
-                if (k < nb) m |= (uint64_t)((fbu[(size_t)(b0 + k) * words] >> sh) & 1u) << k;
+            for (int k = 0; k < nb; ++k) m |= (uint64_t)((fbu[(size_t)(b0 + k) * words] >> sh) & 1u) << k;
             while (m) {
                 int rr[U];
                 uint64_t x[U][P];
@@ -1197,11 +1196,9 @@ __global__ void __launch_bounds__(kThreads) k_flush_packed(Wave w, const int32_t
         uint64_t mk[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int nb = R - 64 * b;
-            if (nb <= 0) continue;
+            const int nb = R - 64 * b < 64 ? R - 64 * b : 64;  // the block's recorded rounds
 #pragma unroll 8
-            for (int k = 0; k < 64; ++k)
-                if (k < nb) mk[b] |= (uint64_t)((fbu[(size_t)(64 * b + k) * words] >> sh) & 1u) << k;
+            for (int k = 0; k < nb; ++k) mk[b] |= (uint64_t)((fbu[(size_t)(64 * b + k) * words] >> sh) & 1u) << k;
         }
         for (int s = 0; s < w.nslots; ++s) {
             const int m0 = s_first[s], mc = s_first[s + 1] - m0;
@@ -1248,9 +1245,10 @@ __global__ void __launch_bounds__(kThreads) k_flush_packed(Wave w, const int32_t
                 M.dist[v] = (uint8_t)dl;
                 for (int j = 0; j < d; ++j) {
                     const int r = dl + j;  // dl == 0xFF: never reached, r > 254 >= R
+                    // the block of round r by selects (an indexed register array would go to memory)
+                    const uint64_t blk = r < 64 ? mk[0] : r < 128 ? mk[1] : r < 192 ? mk[2] : mk[3];
                     uint64_t x = 0;
-                    if (r < R && ((mk[r >> 6] >> (r & 63)) & 1ull))
-                        x = w.hist[((size_t)r * (size_t)n + u) * P + s];
+                    if (r < R && ((blk >> (r & 63)) & 1ull)) x = w.hist[((size_t)r * (size_t)n + u) * P + s];
                     M.masks[(size_t)j * (size_t)n + v] = (x & M.mask) >> M.off;
                 }
             }
