@@ -131,7 +131,9 @@ typedef struct cbfs_tune_s {
        slot word share words (largest first, each into the fullest word with
        room, at most 31 to a word), so a wave traverses as many clusters as
        its words hold; each cluster's outputs are read off its bits of the
-       round records.  Used when it saves words and round records fit.
+       round records.  Used when it saves words and round records fit; the
+       outputs are the same either way.  Calls with host outputs or a label
+       store, and calls with wave_order = 1, keep one cluster per word.
        0 = default (on); < 0 = one cluster per word. */
     int pack;
 } cbfs_tune_t;
