@@ -220,12 +220,21 @@ def measured_peak_hbm():
 
 
 def kernel_source_hash():
+    """Hash of the CUDA sources' code: comments and whitespace are left out,
+    so that a traffic record stays valid across comment-only edits."""
+    import re
+
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2410_17226_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
         if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(csrc, fn), encoding="utf-8") as f:
+                text = f.read()
+            # string literals kept whole, comments dropped, whitespace runs folded
+            code = re.sub(r'("(?:\\.|[^"\\])*")|/\*.*?\*/|//[^\n]*',
+                          lambda m: m.group(1) or " ", text, flags=re.S)
+            h.update(fn.encode())
+            h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

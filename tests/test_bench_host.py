@@ -115,3 +115,19 @@ def test_traffic_of_packed_waves_counts_waves_from_seed_launches(tmp_path):
     assert out["memset_bytes"] == 2 * bench.memset_bytes_per_wave(1000, 4, rows=False)
     assert out["memset_bytes"] == 2 * ((16 * 4 + 4) * 1000 + 2 * 4 * 33 + 288 * 56)
     assert out["per_kernel_bytes"]["cbfs::k_flush_packed<4>"] == int(7e6)
+
+
+def test_kernel_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2410_17226_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    f = csrc / "k.cu"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    f.write_text('__global__ void k(int* x) { x[0] = 1; }\nconst char* s = "a // b";\n')
+    h0 = bench.kernel_source_hash()
+    f.write_text('// a kernel\n__global__ void k(int* x) {  /* one */\n  x[0] = 1;  // store\n}\n'
+                 'const char* s = "a // b";\n')
+    assert bench.kernel_source_hash() == h0
+    f.write_text('__global__ void k(int* x) { x[0] = 2; }\nconst char* s = "a // b";\n')
+    assert bench.kernel_source_hash() != h0
+    f.write_text('__global__ void k(int* x) { x[0] = 1; }\nconst char* s = "a b";\n')
+    assert bench.kernel_source_hash() != h0
