@@ -2010,7 +2010,8 @@ int run_clusters_inner(cbfs_graph_s* g, const int32_t* src, const int32_t* coff,
     // (measured: 0.02 vs 0.08 is 1.5x faster for k = 2..4, equal from k = 8).
     const bool alpha_given = tune && tune->pull_alpha != 0.f;
     const float alpha = alpha_given ? tune->pull_alpha : 0.08f;
-    // order[pos]: the cluster in wave pos / P, slot pos % P (set below)
+    // order[pos]: one cluster per word, the cluster in wave pos / P, slot pos % P;
+    // packed, the order in which clusters go into words (set below)
     std::vector<int> order((size_t)C);
     for (int c = 0; c < C; ++c) order[c] = c;
     // packed waves: the bits used in each slot word (set below); a word's

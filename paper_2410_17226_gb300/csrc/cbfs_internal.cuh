@@ -37,10 +37,14 @@ struct Geo {
 };
 
 // One cluster in flight: where its outputs go.
+// One 64-bit slot word of a wave.  Unpacked: one cluster, its sources in the
+// k low bits, its outputs here.  Packed (the wave's nmembers > 0): several
+// clusters, described by the wave's member table; dist and masks are unused,
+// cluster is the word's first member (wave-local index) and pad its count.
 struct SlotDesc {
     uint8_t* dist;    // output Delta_v, doubles as the "first round" state
     uint64_t* masks;  // output S_v[0..d-1]
-    uint64_t all;     // the k low bits
+    uint64_t all;     // the word's source bits (packed: the union of its members' bits)
     int32_t cluster;
     int32_t pad;
 };
@@ -92,7 +96,7 @@ struct Wave {
     const int32_t* adj;
     int d;
     int P;                  // slots per vertex block (template P of the phase kernels)
-    int nslots;             // clusters in this wave (<= P)
+    int nslots;             // slot words in use in this wave (<= P)
     const SlotDesc* slots;  // device [nslots]
     uint64_t* vis;          // [n][P]
     uint64_t* acc;          // [n][P]
