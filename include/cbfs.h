@@ -118,14 +118,15 @@ typedef struct cbfs_tune_s {
        road grid) gain; on power-law graphs the plain pull is faster.  0 (the
        default) = plain; the autotuner tries both. */
     int fused_pull;
-    /* waves with fused pulls: rounds whose new sources are recorded, one
-       whole block per vertex and round, and turned into the outputs after the
-       wave (each output word written once, together with its neighbours),
-       instead of each output word being written in the round it becomes
-       known; rounds past the recorded ones write directly.  The records take
-       n * clusters-per-wave * 8 + n / 8 bytes of device memory per round.
-       0 = default: as many as fit a quarter of the free device memory, at
-       most 96; > 0 = that many (at most 255); < 0 = none. */
+    /* waves with fused pulls, and packed waves (see pack): rounds whose new
+       sources are recorded, one whole block per vertex and round, and turned
+       into the outputs after the wave (each output word written once,
+       together with its neighbours), instead of each output word being
+       written in the round it becomes known; rounds past the recorded ones
+       write directly.  The records take n * slot-words-per-wave * 8 + n / 8
+       bytes of device memory per round.  0 = default: as many as fit a
+       quarter of the free device memory, at most 96; > 0 = that many (at
+       most 255); < 0 = none (and no packing). */
     int stage_rounds;
     /* calls with device outputs: clusters that fill only part of a 64-bit
        slot word share words (largest first, each into the fullest word with
