@@ -57,8 +57,9 @@ def assert_invariants(dist, masks, clusters):
 
 def test_config2_scale22_256_clusters_batched(cb):
     """Undirected R-MAT scale 22, 256 star clusters of 1..64 sources, d = 2,
-    batched with the autotuned parameters the benchmark uses: all 256
-    clusters equal the oracle."""
+    batched with the autotuned parameters the benchmark uses (clusters packed
+    several to a slot word, the default for device outputs): all 256 clusters
+    equal the oracle."""
     from paper_2410_17226_gb300 import tune
 
     off, adj = I.rmat(22)
